@@ -1,0 +1,22 @@
+"""FP64 CPU oracle for the Stolt-based ASHRT/AASHRT deblending path.
+
+TEST INFRASTRUCTURE ONLY.  Plain, slow, obviously correct numpy code written
+from the thesis (Ibrahim 2015, "Separating simultaneous seismic sources using
+robust inversion of Radon and migration operators").  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference leg
+may import it.  The CUDA library never imports, links or calls anything here,
+and nothing here imports the CUDA library: the two share no code.
+
+Modules
+-------
+dft         naive (matrix) discrete Fourier transforms, the F operators.
+stolt       Stolt-based ASHRT / AASHRT forward and its exact transpose
+            (ch. 5 Eqs ch5_adj_operator / ch5_forward_operator, ch. 6 Eqs
+            ch6_adj_operator / ch6_forward_operator).
+timedomain  time-domain ASHRT / AASHRT hyperbolic summation (ch. 3 Table
+            ch3_table_Radon_operators, ch. 6 Eqs ch6_AASHRT_forward /
+            ch6_AASHRT_adjoint); used as an independent kinematic check.
+irls        robust l_p-l_q inversion by IRLS with inner CGLS (ch. 4 Eqs
+            ch4_cost_fn, equ:10, equ:11, ch4_epcilon_r) and the quality
+            measures Q_PD, Q_R (Eqs ch4_Qpd, ch4_Qr).
+"""
