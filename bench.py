@@ -1,0 +1,302 @@
+"""Benchmark of the Stolt-ASHRT robust deblending hot path on GB300.
+
+Workload (one step): robust IRLS deblending (p = q = 1, 8 outer x 30 CGLS
+iterations, Ricker wavelet C at 25 Hz) of a batch of 64 synthetic
+pseudo-deblended common-receiver gathers, nt = 1024 @ 4 ms, nx = 256 @ 12.5 m,
+Radon scan of 32 velocities x 256 apexes.  Every operator application is a
+Stolt-ASHRT forward or adjoint over the whole batch.
+
+value = gather-level forward+adjoint operator pairs per second over all ranks
+(pairs = batch x (forward applies + adjoint applies) / 2 per step), measured
+with inputs resident in HBM; `gathers_per_s` is deblended gathers per second;
+`e2e` is the same metric through the public API with host buffers (pinned
+host -> device copy of the gathers, device -> host copy of the recovered
+gathers, every step).  `--impl reference` times the FP64 CPU oracle (the
+reference arm of this method) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NT, NX, NV, B = 1024, 256, 32, 64
+DT, DX = 0.004, 12.5
+N_OUTER, N_CG = 8, 30
+F_PEAK = 25.0
+METRIC = "Stolt-ASHRT fwd+adj pairs/s (robust IRLS deblend, 64 gathers 1024x256, 32 velocities)"
+UNIT = "gather fwd+adj pairs/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _config(extra=None):
+    c = {"workload": "robust IRLS deblend, 64 gathers x (nt 1024 @ 4 ms, nx 256 @ 12.5 m), "
+                     "32 velocities x 256 apexes, IRLS 8 x 30, p = q = 1, 25 Hz wavelet",
+         "gathers_per_step": B, "nt": NT, "nx": NX, "nv": NV, "irls": [N_OUTER, N_CG],
+         "padded": [2048, 512], "l2": "inputs larger than L2 (model 2.1 GB per vector)",
+         "parallelism": "replicas (gathers are independent; no collective)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per gather (roofline section)
+def _fft_flops(n):
+    return 5.0 * n * (n.bit_length() - 1)
+
+
+def algorithmic(nt=NT, nx=NX, P=NV, Nt=2048, Nx=512):
+    lh = Nx // 2 + 1
+    rows = (P + 1) * lh * _fft_flops(Nt) + 16.0 * P * Nt * lh          # one row kernel launch, per gather
+    xcols = (P + 1) * nt * 0.5 * _fft_flops(Nx)                         # both trace-axis kernels, per gather
+    pair_flops = 2.0 * (rows + xcols)
+    pair_bytes = 2.0 * 4.0 * nt * nx * (P + 1)
+    return dict(rows_flops=rows, pair_flops=pair_flops, pair_bytes=pair_bytes,
+                rows_bytes=4.0 * 2 * lh * nt * (P + 1))
+
+
+def _peaks():
+    p = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+    except OSError:
+        pass
+    hbm = p.get("hbm_gbs")
+    return dict(hbm_gbs=hbm if hbm else 6800.0, hbm_src="measured" if hbm else "fallback",
+                sm_max_mhz=p.get("sm_max_mhz", 2070.0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_sample():
+    """The FP64 oracle (numpy, naive DFTs) on one gather of the workload: one
+    forward + one adjoint with all 32 velocities, timed on the host cores."""
+    import numpy as np
+
+    from oracle import stolt
+    from paper_1711_10214_gb300 import synth
+    v = synth.velocity_scan(1400.0, 3500.0, NV)
+    g = stolt.Geometry(NT, NX, DT, DX, v, wavelet_peak_hz=F_PEAK)
+    rng = np.random.default_rng(0)
+    m = rng.standard_normal(g.model_shape)
+    d = rng.standard_normal(g.data_shape)
+    t0 = time.perf_counter()
+    stolt.forward(g, m)
+    stolt.adjoint(g, d)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return dict(value=1.0 / dt, unit=UNIT, cores=cores, kind="oracle",
+                sample="1 gather, 1 forward + 1 adjoint (32 velocities, nt 1024, nx 256), "
+                       "FP64 numpy naive-DFT oracle; %.1f s" % dt)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline_sample()
+        if i >= args.warmup:
+            vals.append(r["value"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config({"reference_step": "1 gather fwd+adj pair (bounded sample)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1711_10214_gb300 import ashrt, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    c = synth.config2(B, NT, NX, NV)
+    d_host = torch.from_numpy(c["blended"].astype(np.float32)).pin_memory()
+    drec_host = torch.empty_like(d_host).pin_memory()
+    d = d_host.to(dev)
+    plan = ashrt.Plan(NT, NX, DT, DX, c["velocities"], wavelet_peak_hz=F_PEAK, max_batch=B,
+                      with_solver=True)
+    m = torch.empty((B,) + plan.model_shape, device=dev)
+    drec = torch.empty_like(d)
+    stream = torch.cuda.current_stream(dev)
+    kw = dict(p=1.0, q=1.0, n_outer=N_OUTER, n_cg=N_CG)
+
+    for _ in range(args.warmup):
+        reps = plan.deblend(d, m, drec, batch=B, stream=stream, **kw)
+    torch.cuda.synchronize(dev)
+    pairs_per_step = B * (reps[0]["applies_fwd"] + reps[0]["applies_adj"]) / 2.0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ashrt.profile_read()
+    ashrt.profile_enable(True)
+    launches0 = ashrt.kernel_launches()
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        reps = plan.deblend(d, m, drec, batch=B, stream=stream, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = ashrt.kernel_launches() - launches0
+    ashrt.profile_enable(False)
+    prof = ashrt.profile_read()
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1000.0
+    if dist is not None:
+        tt = torch.tensor([t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = world * pairs_per_step * args.steps / t
+
+    # end to end through the public API with host buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        d.copy_(d_host, non_blocking=True)
+        plan.deblend(d, m, drec, batch=B, stream=stream, **kw)
+        drec_host.copy_(drec, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    te = time.perf_counter() - t0
+    barrier()
+    e2e = world * pairs_per_step * e2e_steps / te
+
+    if rank != 0:
+        return
+    alg = algorithmic()
+    pk = _peaks()
+    dom = max(("stolt_fwd_rows", "stolt_adj_rows", "xfft_r2c", "xfft_c2r"),
+              key=lambda k: prof[k][0])
+    ms, cnt = prof[dom]
+    per_launch_s = ms / 1000.0 / max(cnt, 1)
+    alu_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s, FP32 FMA lanes at max clock
+    if dom.startswith("stolt"):
+        flops = alg["rows_flops"] * B
+    else:
+        flops = (NV + 1) * NT * 0.5 * _fft_flops(512) * B
+    achieved = flops / per_launch_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(),
+        "gathers_per_s": world * B * args.steps / t,
+        "hbm_fraction_pair": {"algorithmic_bytes_per_pair": alg["pair_bytes"],
+                              "achieved_gbs": value / world * alg["pair_bytes"] / 1e9,
+                              "peak_gbs": pk["hbm_gbs"], "peak_src": pk["hbm_src"]},
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                     "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"},
+        "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items()},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(d_host.numel() * 4),
+                "d2h_bytes_per_step": int(drec_host.numel() * 4)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "gpu": torch.cuda.get_device_name(dev),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * ashrt.h -- C ABI of the GB300 (sm_103a) Stolt-based apex-shifted hyperbolic
+ * Radon transform (ASHRT), its asymptote-shifted extension (AASHRT), and the
+ * robust IRLS deblending solve built on them.
+ *
+ * Method: Ibrahim (2015), "Separating simultaneous seismic sources using
+ * robust inversion of Radon and migration operators" (arxiv 1711.10214).
+ *   ch. 5, Eqs ch5_forward_operator / ch5_adj_operator: L = S F^-1 M F,
+ *          L^T = F^-1 M^T F S^T (Stolt map M, sum S over velocities);
+ *   ch. 6, Eqs ch6_forward_operator / ch6_adj_operator: adds the asymptote
+ *          time shift T = exp(-i w tau0), the sum A over (v, tau0) and the
+ *          trace-sampling operator S;
+ *   ch. 4, Eqs ch4_cost_fn, equ:10, equ:11, ch4_epcilon_r: robust l_p-l_q
+ *          inversion by IRLS with an inner conjugate-gradient (CGLS) solve.
+ *
+ * Conventions shared by every call
+ *   - Data (a common-receiver gather) is float32 [batch][nx][nt], t fastest.
+ *   - Model is float32 [batch][nt0][nv][nx][nt]: one (tau, x_apex) panel per
+ *     (asymptote shift tau0_j, velocity v_i), t (= tau) fastest.  Apex
+ *     positions equal trace positions (x_a == x, ch. 6).
+ *   - All array arguments named *_dev are device pointers owned by the
+ *     caller, contiguous, 4-byte aligned; nothing here frees them.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream) unless documented otherwise.  Calls never
+ *     allocate device memory except ashrt_plan_create.
+ *   - Functions return an ashrt_status; no exception crosses the ABI.  The
+ *     text of the last error of the calling thread is ashrt_last_error().
+ *   - A plan may be used from one thread at a time: forward, adjoint and the
+ *     deblend solve all use the plan's workspace.
+ */
+#ifndef ASHRT_H
+#define ASHRT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ASHRT_OK = 0,
+  ASHRT_EINVAL = 1,     /* invalid argument (sizes, NULL pointers, grids) */
+  ASHRT_ENOMEM = 2,     /* device allocation failed at plan creation */
+  ASHRT_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  ASHRT_ENAN = 4,       /* non-finite value in the input data */
+  ASHRT_ENOTCONV = 5,   /* IRLS stopped without meeting its tolerance (informative) */
+  ASHRT_ETIMEOUT = 6,   /* a device-side bounded wait ran out */
+  ASHRT_EINTERNAL = 7   /* internal consistency check failed */
+} ashrt_status;
+
+typedef struct ashrt_plan ashrt_plan;
+
+/* Operator options (ch. 5 "zero padding"; ch. 4 wavelet C; ch. 5 band limit). */
+typedef struct {
+  int pad_t;              /* Nt = next power of two >= pad_t * nt (default 2) */
+  int pad_x;              /* Nx = next power of two >= pad_x * nx (default 2) */
+  float fmax_hz;          /* > 0: zero |f| > fmax in both directions; 0 = none */
+  float wavelet_peak_hz;  /* > 0: apply the zero-phase Ricker amplitude spectrum
+                             W(f) = (f/fp)^2 exp(1 - (f/fp)^2) as C (forward) and
+                             C^T (adjoint); 0 = off */
+  int max_batch;          /* largest batch any call will pass (workspace size) */
+  int with_solver;        /* 1: also allocate the IRLS/CGLS vectors */
+} ashrt_opts;
+
+/* Fills *opts with the defaults: pad 2/2, no band limit, no wavelet,
+ * max_batch 1, with_solver 0. */
+void ashrt_default_opts(ashrt_opts* opts);
+
+/*
+ * Creates a plan on the current CUDA device.
+ *   nt, nx        samples per trace and traces per gather (nt >= 2, nx >= 2,
+ *                 Nt <= 4096, Nx <= 2048 after padding)
+ *   dt, dx        sample interval [s] and trace spacing [m]
+ *   velocities    host array of nv > 0 scan velocities [m/s] (>= 0)
+ *   apex_x        host array of napex apex positions [m]; must be NULL or the
+ *                 trace positions j*dx (napex == nx): the Stolt operator
+ *                 requires x_a == x (ch. 6)
+ *   t0_shifts     host array of nt0 asymptote shifts tau0 [s], or NULL with
+ *                 nt0 = 1 for plain ASHRT (tau0 = 0, ch. 6: AASHRT reduces to
+ *                 ASHRT at zero shift)
+ *   opts          may be NULL (defaults)
+ * The cone membership of every (w, k_x) bin is decided on the host in IEEE
+ * double as k*k > a*a with a = ((v*|l|)*Nt)*dt/(Nx*dx) (bin units).
+ * Allocates all device tables and workspace; returns ASHRT_ENOMEM if that
+ * fails.  *out receives the plan (NULL on failure).
+ */
+ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, double dx,
+                               const float* velocities, int nv,
+                               const float* apex_x, int napex,
+                               const float* t0_shifts, int nt0,
+                               const ashrt_opts* opts);
+
+/* Frees a plan and its device memory (synchronises the device first). NULL is a no-op. */
+void ashrt_plan_destroy(ashrt_plan* plan);
+
+/* Reports padded sizes, panel count P = nv*nt0 and the workspace held. Any out pointer may be NULL. */
+ashrt_status ashrt_plan_info(const ashrt_plan* plan, int* Nt, int* Nx, int* n_panels,
+                             size_t* workspace_bytes);
+
+/*
+ * Forward (demigration / modelling), ch. 5 Eq. ch5_forward_operator and
+ * ch. 6 Eq. ch6_forward_operator:
+ *   d = S C F^-1 sum_{tau0} T(tau0) sum_v M_v F m,   T = exp(-i w tau0).
+ *   m_dev           [batch][nt0][nv][nx][nt] float32 model (read)
+ *   d_dev           [batch][nx][nt] float32 data (written)
+ *   trace_mask_dev  [batch][nx] float32 sampling weights S (1 keep, 0 drop) or NULL
+ * batch must be in [1, max_batch].  Uses the plan workspace.
+ */
+ashrt_status ashrt_forward(const ashrt_plan* plan, const float* m_dev, float* d_dev,
+                           const float* trace_mask_dev, int batch, void* stream);
+
+/*
+ * Adjoint (migration), ch. 5 Eq. ch5_adj_operator and ch. 6 Eq.
+ * ch6_adj_operator: the exact transpose of ashrt_forward (linear-interpolation
+ * weights transposed, conjugate phase), so <L m, d> = <m, L^T d> to rounding.
+ *   d_dev  [batch][nx][nt] (read);  m_dev [batch][nt0][nv][nx][nt] (written)
+ */
+ashrt_status ashrt_adjoint(const ashrt_plan* plan, const float* d_dev, float* m_dev,
+                           const float* trace_mask_dev, int batch, void* stream);
+
+/* Options of the robust solve (ch. 4). */
+typedef struct {
+  double p;               /* misfit norm exponent, 0 < p <= 2 (1 = robust) */
+  double q;               /* model norm exponent, 0 < q <= 2 (1 = sparse) */
+  int n_outer;            /* IRLS (reweighting) iterations, <= 64 */
+  int n_cg;               /* CGLS iterations per outer iteration */
+  double tol;             /* stop a gather when |J_k - J_k-1| / J_k-1 < tol; 0 = never */
+  double b_r;             /* eps_r = b_r MAD(r) / 0.6745 (default 1.345) */
+  double b_m;             /* eps_m = b_m max|m| / 100 (default 1) */
+  double mu;              /* trade-off of Eq. equ:11 (default 0: CG count regularises) */
+  int warm_start_cg;      /* 1: start CGLS of outer k from u0 = W_m m_{k-1} (default 1) */
+  double eps_r_fixed;     /* > 0: use this eps_r instead of the MAD rule */
+  double eps_m_fixed;     /* > 0: use this eps_m instead of the max rule */
+  const float* trace_mask_dev;  /* [batch][nx] sampling weights S, or NULL */
+} irls_opts;
+
+/* Per-gather outcome of the robust solve. */
+typedef struct {
+  int outer_done;         /* outer iterations actually run for this gather */
+  int applies_fwd;        /* forward operator applications spent on it */
+  int applies_adj;        /* adjoint operator applications spent on it */
+  int flags;              /* bit 0: stopped on tol; bit 1: breakdown (zero CG denominator) */
+  double misfit[64];      /* J_k = sum |r_i|^p over live samples after outer k (FP64) */
+} irls_report;
+
+/* Fills *opts with p = q = 1, n_outer 5, n_cg 20, tol 0, b_r 1.345, b_m 1, mu 0, warm start on. */
+void irls_default_opts(irls_opts* opts);
+
+/*
+ * Robust Radon deblending of `batch` gathers (ch. 4, Eqs ch4_cost_fn, equ:10,
+ * equ:11): minimise ||d - C S L m||_p^p + mu ||m||_q^q by IRLS; each outer
+ * iteration sets W_r, W_m from the residual and model (eps_r from the MAD,
+ * eps_m from max|m|; W = I at the first), then runs CGLS on
+ * A = W_r S C L W_m^-1 with u = W_m m.  CG scalars and all norms are
+ * accumulated in FP64, per gather.
+ *   d_dev     [batch][nx][nt] pseudo-deblended gathers (read)
+ *   m_dev     [batch][nt0][nv][nx][nt] Radon models (written)
+ *   drec_dev  [batch][nx][nt] recovered gathers C L m, no mask (written; may be NULL)
+ *   per_gather  host array of `batch` reports (may be NULL)
+ * Requires a plan created with with_solver = 1.  Synchronises `stream` once
+ * at the end (and once per outer iteration when tol > 0).  Returns
+ * ASHRT_ENAN if d holds a non-finite value (m and drec are then untouched).
+ */
+ashrt_status robust_irls_deblend(const ashrt_plan* plan, const float* d_dev, float* m_dev,
+                                 float* drec_dev, int batch, const irls_opts* opts,
+                                 irls_report* per_gather, void* stream);
+
+/*
+ * Measurement hooks (no counterpart in the paper; used to time the library's
+ * own kernels on the streams they run on).
+ *   ashrt_profile_enable(1): from now on every operator kernel launch is
+ *     bracketed by two CUDA events recorded on its stream (cheap, but not free).
+ *   ashrt_profile_read: synchronises on the recorded events and returns, per
+ *     kernel class, the summed elapsed milliseconds and the number of timed
+ *     launches since the previous read, then resets them.  Classes:
+ *     0 trace-axis r2c FFT, 1 forward row kernel (t-FFT + Stolt map + sum),
+ *     2 adjoint row kernel, 3 trace-axis c2r FFT, 4 solver vector kernels
+ *     (counted only).  n is the length of ms / launches (up to 5).
+ *     Returns 0, or 1 if an event could not be read.
+ *   ashrt_kernel_launches: total kernels this library has launched in the
+ *     process (all classes, profiling on or off).
+ */
+void ashrt_profile_enable(int on);
+int ashrt_profile_read(double* ms, long long* launches, int n);
+long long ashrt_kernel_launches(void);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* ashrt_last_error(void);
+
+/* Static name of a status code. */
+const char* ashrt_status_string(ashrt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASHRT_H */

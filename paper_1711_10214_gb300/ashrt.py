@@ -1,0 +1,223 @@
+"""ctypes binding of libashrt (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts Python
+arguments (torch CUDA tensors or raw device addresses, host float arrays) to
+the C ABI of ``include/ashrt.h`` and raises ``AshrtError`` on a non-OK status.
+There is no fallback: if the library is missing, ``load()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libashrt.so")
+
+c_int, c_float, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_float, ctypes.c_double,
+                                                 ctypes.c_void_p, ctypes.c_size_t)
+
+STATUS = {0: "ASHRT_OK", 1: "ASHRT_EINVAL", 2: "ASHRT_ENOMEM", 3: "ASHRT_ECUDA",
+          4: "ASHRT_ENAN", 5: "ASHRT_ENOTCONV", 6: "ASHRT_ETIMEOUT", 7: "ASHRT_EINTERNAL"}
+
+
+class AshrtOpts(ctypes.Structure):
+    _fields_ = [("pad_t", c_int), ("pad_x", c_int), ("fmax_hz", c_float),
+                ("wavelet_peak_hz", c_float), ("max_batch", c_int), ("with_solver", c_int)]
+
+
+class IrlsOpts(ctypes.Structure):
+    _fields_ = [("p", c_double), ("q", c_double), ("n_outer", c_int), ("n_cg", c_int),
+                ("tol", c_double), ("b_r", c_double), ("b_m", c_double), ("mu", c_double),
+                ("warm_start_cg", c_int), ("eps_r_fixed", c_double), ("eps_m_fixed", c_double),
+                ("trace_mask_dev", c_void_p)]
+
+
+class IrlsReport(ctypes.Structure):
+    _fields_ = [("outer_done", c_int), ("applies_fwd", c_int), ("applies_adj", c_int),
+                ("flags", c_int), ("misfit", c_double * 64)]
+
+
+class AshrtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libashrt.so (built in-tree by ``build.py``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libashrt.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    try:  # the library links the shared CUDA runtime that torch has already loaded
+        import torch  # noqa: F401
+    except ImportError:
+        pass
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    lib.ashrt_default_opts.argtypes = [P(AshrtOpts)]
+    lib.ashrt_default_opts.restype = None
+    lib.irls_default_opts.argtypes = [P(IrlsOpts)]
+    lib.irls_default_opts.restype = None
+    lib.ashrt_plan_create.argtypes = [P(c_void_p), c_int, c_int, c_double, c_double,
+                                      P(c_float), c_int, P(c_float), c_int, P(c_float), c_int,
+                                      P(AshrtOpts)]
+    lib.ashrt_plan_create.restype = c_int
+    lib.ashrt_plan_destroy.argtypes = [c_void_p]
+    lib.ashrt_plan_destroy.restype = None
+    lib.ashrt_plan_info.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int), P(c_size_t)]
+    lib.ashrt_plan_info.restype = c_int
+    for name in ("ashrt_forward", "ashrt_adjoint"):
+        f = getattr(lib, name)
+        f.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]
+        f.restype = c_int
+    lib.robust_irls_deblend.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                                        P(IrlsOpts), P(IrlsReport), c_void_p]
+    lib.robust_irls_deblend.restype = c_int
+    lib.ashrt_last_error.argtypes = []
+    lib.ashrt_last_error.restype = ctypes.c_char_p
+    lib.ashrt_profile_enable.argtypes = [c_int]
+    lib.ashrt_profile_enable.restype = None
+    lib.ashrt_profile_read.argtypes = [ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong),
+                                       c_int]
+    lib.ashrt_profile_read.restype = c_int
+    lib.ashrt_kernel_launches.argtypes = []
+    lib.ashrt_kernel_launches.restype = ctypes.c_longlong
+    lib.ashrt_status_string.argtypes = [c_int]
+    lib.ashrt_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise AshrtError(status, load().ashrt_last_error().decode())
+
+
+def _ptr(x):
+    """Device address of a torch tensor (checked contiguous float32) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda or x.dtype.itemsize != 4 or not x.is_contiguous():
+        raise ValueError("expected a contiguous 4-byte CUDA tensor")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _farr(x):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32).ravel())
+    return a, a.ctypes.data_as(ctypes.POINTER(c_float))
+
+
+PROFILE_CLASSES = ("xfft_r2c", "stolt_fwd_rows", "stolt_adj_rows", "xfft_c2r", "solver")
+
+
+def profile_enable(on=True):
+    load().ashrt_profile_enable(1 if on else 0)
+
+
+def profile_read():
+    """{class: (total_ms, launches)} since the previous read (see ashrt_profile_read)."""
+    ms = (c_double * 5)()
+    cnt = (ctypes.c_longlong * 5)()
+    st = load().ashrt_profile_read(ms, cnt, 5)
+    if st != 0:
+        raise AshrtError(7, "profile events could not be read")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(PROFILE_CLASSES)}
+
+
+def kernel_launches():
+    return int(load().ashrt_kernel_launches())
+
+
+class Plan:
+    """A Stolt ASHRT/AASHRT plan (see ashrt_plan_create in include/ashrt.h)."""
+
+    def __init__(self, nt, nx, dt, dx, velocities, t0s=None, apex_x=None, pad_t=2, pad_x=2,
+                 fmax_hz=0.0, wavelet_peak_hz=0.0, max_batch=1, with_solver=False):
+        lib = load()
+        o = AshrtOpts()
+        lib.ashrt_default_opts(ctypes.byref(o))
+        o.pad_t, o.pad_x = int(pad_t), int(pad_x)
+        o.fmax_hz, o.wavelet_peak_hz = float(fmax_hz), float(wavelet_peak_hz)
+        o.max_batch, o.with_solver = int(max_batch), int(bool(with_solver))
+        self._v, vp = _farr(velocities)
+        if t0s is None:
+            self._t0, tp, nt0 = None, None, 1
+        else:
+            self._t0, tp = _farr(t0s)
+            nt0 = self._t0.size
+        if apex_x is None:
+            ap, na = None, 0
+        else:
+            self._ax, ap = _farr(apex_x)
+            na = self._ax.size
+        h = c_void_p()
+        self._h = None
+        _check(lib.ashrt_plan_create(ctypes.byref(h), int(nt), int(nx), float(dt), float(dx),
+                                     vp, self._v.size, ap, na, tp, nt0, ctypes.byref(o)))
+        self._h = h.value
+        self.nt, self.nx, self.nv, self.nt0 = int(nt), int(nx), self._v.size, nt0
+        self.max_batch = int(max_batch)
+        Nt, Nx, P, ws = c_int(), c_int(), c_int(), c_size_t()
+        _check(lib.ashrt_plan_info(self._h, ctypes.byref(Nt), ctypes.byref(Nx), ctypes.byref(P),
+                                   ctypes.byref(ws)))
+        self.Nt, self.Nx, self.P, self.workspace_bytes = Nt.value, Nx.value, P.value, ws.value
+
+    @property
+    def model_shape(self):
+        return (self.nt0, self.nv, self.nx, self.nt)
+
+    @property
+    def data_shape(self):
+        return (self.nx, self.nt)
+
+    def forward(self, m, d, mask=None, batch=1, stream=None):
+        _check(load().ashrt_forward(self._h, _ptr(m), _ptr(d), _ptr(mask), int(batch),
+                                    _stream(stream)))
+
+    def adjoint(self, d, m, mask=None, batch=1, stream=None):
+        _check(load().ashrt_adjoint(self._h, _ptr(d), _ptr(m), _ptr(mask), int(batch),
+                                    _stream(stream)))
+
+    def deblend(self, d, m, drec=None, batch=1, stream=None, mask=None, **kw):
+        """robust_irls_deblend; keyword options are irls_opts fields. Returns reports."""
+        lib = load()
+        o = IrlsOpts()
+        lib.irls_default_opts(ctypes.byref(o))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError("unknown irls option %r" % k)
+            setattr(o, k, v)
+        o.trace_mask_dev = _ptr(mask)
+        reps = (IrlsReport * int(batch))()
+        _check(lib.robust_irls_deblend(self._h, _ptr(d), _ptr(m), _ptr(drec), int(batch),
+                                       ctypes.byref(o), reps, _stream(stream)))
+        return [dict(outer_done=r.outer_done, applies_fwd=r.applies_fwd,
+                     applies_adj=r.applies_adj, flags=r.flags,
+                     misfit=list(r.misfit[:r.outer_done])) for r in reps]
+
+    def close(self):
+        if self._h:
+            load().ashrt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,100 @@
+// Host-side declarations shared by the translation units of libashrt.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "ashrt.h"
+
+namespace ashrt {
+
+// Arguments of the x-direction (trace-axis) transforms.  One "slab" is one
+// [nx][nt] real panel and its [Lh][ld] complex half spectrum in k_x.
+struct XfftArgs {
+  const float* in_real = nullptr;    // r2c input  [slabs][nx][nt]
+  float2* out_cplx = nullptr;        // r2c output [slabs][Lh][ld]
+  const float2* in_cplx = nullptr;   // c2r input  [slabs][Lh][ld]
+  float* out_real = nullptr;         // c2r output [slabs][nx][nt]
+  int nx = 0, nt = 0, ld = 0, Lh = 0, Nx = 0;
+  long long slab_real = 0;           // nx * nt
+  long long slab_cplx = 0;           // Lh * ld
+  const float* ew = nullptr;         // elementwise weight on the real side, or null
+  const float* tmask = nullptr;      // per-trace weight [gather][nx], or null
+  int slabs_per_gather = 1;
+  double* dot = nullptr;             // c2r: per-gather sum of squared outputs (added), or null
+  const float2* tw = nullptr;        // base twiddles of length Nx
+  int slabs = 0;
+};
+
+// Arguments of the fused t-FFT + Stolt map + sum/spray row kernels.
+struct RowArgs {
+  const float2* X = nullptr;   // model spectra [B][P][Lh][ld]  (fwd in / adj out)
+  float2* Xw = nullptr;
+  const float2* Y = nullptr;   // data spectrum [B][Lh][ld]     (adj in / fwd out)
+  float2* Yw = nullptr;
+  int nt = 0, ld = 0, Lh = 0, P = 0, nv = 0, nt0 = 0, Nt = 0;
+  long long x_batch = 0, x_panel = 0, y_batch = 0;
+  const float2* tw = nullptr;      // base twiddles of length Nt
+  const float* wt = nullptr;       // [Nt] spectral weight W(w)/(Nt Nx), 0 at unmapped bins
+  const int* kmin = nullptr;       // [nv][Lh] first mapped |k| (host FP64 cone rule)
+  const float2* acone = nullptr;   // [nv][Lh] cone parameter a as (hi, lo) floats
+  const float2* phase = nullptr;   // [nt0][Nt] exp(-i w tau0), or null (tau0 == 0)
+  int batch = 0;
+};
+
+cudaError_t launch_xfft_r2c(const XfftArgs& a, cudaStream_t s);
+cudaError_t launch_xfft_c2r(const XfftArgs& a, cudaStream_t s);
+cudaError_t launch_stolt_fwd_rows(const RowArgs& a, cudaStream_t s);
+cudaError_t launch_stolt_adj_rows(const RowArgs& a, cudaStream_t s);
+
+// Twiddle tables in the layout the device passes expect (see common.cuh).
+int twiddle_table_len(int logn);
+void build_twiddle_table(int logn, float2* out);
+
+void set_error(const char* fmt, ...);
+
+// Launch accounting / optional event timing per kernel class (prof.cu).
+enum ProfClass { PROF_XR2C = 0, PROF_ROWS_FWD = 1, PROF_ROWS_ADJ = 2, PROF_XC2R = 3,
+                 PROF_SOLVER = 4, kProfClasses = 5 };
+void prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, cudaStream_t s);
+void count_launches(int n);
+
+}  // namespace ashrt
+
+// The plan (opaque to users).
+struct ashrt_plan {
+  int device = 0;
+  int nt = 0, nx = 0, nv = 0, nt0 = 0, P = 0;
+  double dt = 0, dx = 0;
+  int Nt = 0, Nx = 0, Lh = 0, ld = 0, logNt = 0, logNx = 0;
+  int max_batch = 1;
+  int with_solver = 0;
+  ashrt_opts opts{};
+  bool shift = false;        // any nonzero tau0
+  // device tables
+  float2* tw_t = nullptr;
+  float2* tw_x = nullptr;
+  float* wt = nullptr;
+  int* kmin = nullptr;
+  float2* acone = nullptr;
+  float2* phase = nullptr;
+  // workspace
+  float2* X = nullptr;       // [max_batch][P][Lh][ld]
+  float2* Y = nullptr;       // [max_batch][Lh][ld]
+  size_t ws_bytes = 0;
+  // solver vectors (with_solver)
+  float* u = nullptr;        // model-sized
+  float* pv = nullptr;       // model-sized
+  float* sv = nullptr;       // model-sized
+  float* wminv = nullptr;    // model-sized
+  float* r = nullptr;        // data-sized
+  float* qv = nullptr;       // data-sized
+  float* wr = nullptr;       // data-sized
+  float* y = nullptr;        // data-sized
+  double* scal = nullptr;    // per-gather scalars
+  unsigned int* sel = nullptr;   // per-gather selection scratch
+  int* flags = nullptr;      // per-gather status flags
+};

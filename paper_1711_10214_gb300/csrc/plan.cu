@@ -1,0 +1,499 @@
+// Plan creation (host tables in FP64), the operator pair ashrt_forward /
+// ashrt_adjoint, and the ABI's error plumbing.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "ops.h"
+
+namespace ashrt {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+static int ilog2_ceil(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// Base twiddles exp(-2 pi i k / (Ns R)), k < Ns, for every pass of a
+// length-2^logn Stockham schedule (radix 8 passes, then one radix 2 or 4).
+int twiddle_table_len(int logn) {
+  int n8 = logn / 3, rl = 1 << (logn % 3), np = n8 + (rl > 1 ? 1 : 0);
+  int len = 0, ns = 1;
+  for (int q = 0; q < np; ++q) {
+    len += ns;
+    ns *= (q < n8 ? 8 : rl);
+  }
+  return len;
+}
+
+void build_twiddle_table(int logn, float2* out) {
+  int n8 = logn / 3, rl = 1 << (logn % 3), np = n8 + (rl > 1 ? 1 : 0);
+  int off = 0, ns = 1;
+  for (int q = 0; q < np; ++q) {
+    const int R = q < n8 ? 8 : rl;
+    for (int k = 0; k < ns; ++k) {
+      const double ang = -2.0 * M_PI * (double)k / (double)(ns * R);
+      out[off + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    off += ns;
+    ns *= R;
+  }
+}
+
+static ashrt_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return ASHRT_ECUDA;
+}
+
+#define ASHRT_CUDA(call, what)                         \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+static void free_plan_memory(ashrt_plan* p) {
+  void* ptrs[] = {p->tw_t, p->tw_x, p->wt, p->kmin, p->acone, p->phase, p->X, p->Y,
+                  p->u, p->pv, p->sv, p->wminv, p->r, p->qv, p->wr, p->y,
+                  p->scal, p->sel, p->flags};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+template <typename T>
+static ashrt_status dev_alloc(T** ptr, size_t count, size_t* total) {
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)ptr, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    return ASHRT_ENOMEM;
+  }
+  if (total) *total += bytes;
+  return ASHRT_OK;
+}
+
+template <typename T>
+static ashrt_status upload(T** ptr, const std::vector<T>& host, size_t* total) {
+  ashrt_status st = dev_alloc(ptr, host.size(), total);
+  if (st != ASHRT_OK) return st;
+  cudaError_t e = cudaMemcpy(*ptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (plan tables)");
+  return ASHRT_OK;
+}
+
+size_t model_elems(const ashrt_plan* p) { return (size_t)p->P * p->nx * p->nt; }
+size_t data_elems(const ashrt_plan* p) { return (size_t)p->nx * p->nt; }
+
+// ---------------------------------------------------------------------------
+// Operator application with the fused IRLS weights.
+//   forward: d = tmask * ew_data * L(ew_model * m); dot[g] += ||d_g||^2
+//   adjoint: m = ew_model * L^T(tmask * ew_data * d); dot[g] += ||m_g||^2
+cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const float* ew_model,
+                       const float* ew_data, const float* tmask, double* dot, int batch,
+                       cudaStream_t s) {
+  XfftArgs ax;
+  ax.in_real = m;
+  ax.out_cplx = p->X;
+  ax.nx = p->nx;
+  ax.nt = p->nt;
+  ax.ld = p->ld;
+  ax.Lh = p->Lh;
+  ax.Nx = p->Nx;
+  ax.slab_real = (long long)p->nx * p->nt;
+  ax.slab_cplx = (long long)p->Lh * p->ld;
+  ax.ew = ew_model;
+  ax.slabs_per_gather = p->P;
+  ax.slabs = batch * p->P;
+  ax.tw = p->tw_x;
+  prof_begin(PROF_XR2C, s);
+  cudaError_t e = launch_xfft_r2c(ax, s);
+  prof_end(PROF_XR2C, s);
+  if (e != cudaSuccess) return e;
+
+  RowArgs ra;
+  ra.X = p->X;
+  ra.Yw = p->Y;
+  ra.nt = p->nt;
+  ra.ld = p->ld;
+  ra.Lh = p->Lh;
+  ra.P = p->P;
+  ra.nv = p->nv;
+  ra.nt0 = p->nt0;
+  ra.Nt = p->Nt;
+  ra.x_panel = (long long)p->Lh * p->ld;
+  ra.x_batch = ra.x_panel * p->P;
+  ra.y_batch = ra.x_panel;
+  ra.tw = p->tw_t;
+  ra.wt = p->wt;
+  ra.kmin = p->kmin;
+  ra.acone = p->acone;
+  ra.phase = p->shift ? p->phase : nullptr;
+  ra.batch = batch;
+  prof_begin(PROF_ROWS_FWD, s);
+  e = launch_stolt_fwd_rows(ra, s);
+  prof_end(PROF_ROWS_FWD, s);
+  if (e != cudaSuccess) return e;
+
+  XfftArgs ay = ax;
+  ay.in_cplx = p->Y;
+  ay.out_real = d;
+  ay.ew = ew_data;
+  ay.tmask = tmask;
+  ay.slabs_per_gather = 1;
+  ay.slabs = batch;
+  ay.dot = dot;
+  prof_begin(PROF_XC2R, s);
+  e = launch_xfft_c2r(ay, s);
+  prof_end(PROF_XC2R, s);
+  return e;
+}
+
+cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const float* ew_model,
+                       const float* ew_data, const float* tmask, double* dot, int batch,
+                       cudaStream_t s) {
+  XfftArgs ay;
+  ay.in_real = d;
+  ay.out_cplx = p->Y;
+  ay.nx = p->nx;
+  ay.nt = p->nt;
+  ay.ld = p->ld;
+  ay.Lh = p->Lh;
+  ay.Nx = p->Nx;
+  ay.slab_real = (long long)p->nx * p->nt;
+  ay.slab_cplx = (long long)p->Lh * p->ld;
+  ay.ew = ew_data;
+  ay.tmask = tmask;
+  ay.slabs_per_gather = 1;
+  ay.slabs = batch;
+  ay.tw = p->tw_x;
+  prof_begin(PROF_XR2C, s);
+  cudaError_t e = launch_xfft_r2c(ay, s);
+  prof_end(PROF_XR2C, s);
+  if (e != cudaSuccess) return e;
+
+  RowArgs ra;
+  ra.Y = p->Y;
+  ra.Xw = p->X;
+  ra.nt = p->nt;
+  ra.ld = p->ld;
+  ra.Lh = p->Lh;
+  ra.P = p->P;
+  ra.nv = p->nv;
+  ra.nt0 = p->nt0;
+  ra.Nt = p->Nt;
+  ra.x_panel = (long long)p->Lh * p->ld;
+  ra.x_batch = ra.x_panel * p->P;
+  ra.y_batch = ra.x_panel;
+  ra.tw = p->tw_t;
+  ra.wt = p->wt;
+  ra.kmin = p->kmin;
+  ra.acone = p->acone;
+  ra.phase = p->shift ? p->phase : nullptr;
+  ra.batch = batch;
+  prof_begin(PROF_ROWS_ADJ, s);
+  e = launch_stolt_adj_rows(ra, s);
+  prof_end(PROF_ROWS_ADJ, s);
+  if (e != cudaSuccess) return e;
+
+  XfftArgs ax = ay;
+  ax.in_cplx = p->X;
+  ax.out_real = m;
+  ax.ew = ew_model;
+  ax.tmask = nullptr;
+  ax.slabs_per_gather = p->P;
+  ax.slabs = batch * p->P;
+  ax.dot = dot;
+  prof_begin(PROF_XC2R, s);
+  e = launch_xfft_c2r(ax, s);
+  prof_end(PROF_XC2R, s);
+  return e;
+}
+
+}  // namespace ashrt
+
+using namespace ashrt;
+
+extern "C" {
+
+void ashrt_default_opts(ashrt_opts* o) {
+  if (!o) return;
+  o->pad_t = 2;
+  o->pad_x = 2;
+  o->fmax_hz = 0.f;
+  o->wavelet_peak_hz = 0.f;
+  o->max_batch = 1;
+  o->with_solver = 0;
+}
+
+const char* ashrt_last_error(void) { return g_err.c_str(); }
+
+const char* ashrt_status_string(ashrt_status s) {
+  switch (s) {
+    case ASHRT_OK: return "ASHRT_OK";
+    case ASHRT_EINVAL: return "ASHRT_EINVAL";
+    case ASHRT_ENOMEM: return "ASHRT_ENOMEM";
+    case ASHRT_ECUDA: return "ASHRT_ECUDA";
+    case ASHRT_ENAN: return "ASHRT_ENAN";
+    case ASHRT_ENOTCONV: return "ASHRT_ENOTCONV";
+    case ASHRT_ETIMEOUT: return "ASHRT_ETIMEOUT";
+    case ASHRT_EINTERNAL: return "ASHRT_EINTERNAL";
+  }
+  return "ASHRT_UNKNOWN";
+}
+
+ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, double dx,
+                               const float* velocities, int nv, const float* apex_x, int napex,
+                               const float* t0_shifts, int nt0, const ashrt_opts* opts) {
+  g_err.clear();
+  if (!out) {
+    set_error("plan_create: out is NULL");
+    return ASHRT_EINVAL;
+  }
+  *out = nullptr;
+  ashrt_opts o;
+  ashrt_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.pad_t <= 0) o.pad_t = 2;
+  if (o.pad_x <= 0) o.pad_x = 2;
+  if (o.max_batch <= 0) o.max_batch = 1;
+  if (nt < 2 || nx < 2 || !(dt > 0) || !(dx > 0) || nv <= 0 || !velocities) {
+    set_error("plan_create: need nt >= 2, nx >= 2, dt > 0, dx > 0, nv > 0 and velocities");
+    return ASHRT_EINVAL;
+  }
+  for (int i = 0; i < nv; ++i)
+    if (!(velocities[i] >= 0.f) || !std::isfinite(velocities[i])) {
+      set_error("plan_create: velocity %d is negative or not finite", i);
+      return ASHRT_EINVAL;
+    }
+  if (apex_x) {
+    if (napex != nx) {
+      set_error("plan_create: the Stolt operator needs one apex per trace (napex == nx)");
+      return ASHRT_EINVAL;
+    }
+    for (int j = 0; j < nx; ++j)
+      if (std::fabs((double)apex_x[j] - j * dx) > 1e-3 * dx) {
+        set_error("plan_create: apex %d is not at trace position %g (x_a must equal x)", j, j * dx);
+        return ASHRT_EINVAL;
+      }
+  }
+  if (t0_shifts == nullptr) {
+    if (nt0 != 1 && nt0 != 0) {
+      set_error("plan_create: t0_shifts NULL requires nt0 = 1");
+      return ASHRT_EINVAL;
+    }
+    nt0 = 1;
+  } else if (nt0 <= 0) {
+    set_error("plan_create: nt0 must be positive");
+    return ASHRT_EINVAL;
+  } else {
+    for (int j = 0; j < nt0; ++j)
+      if (!std::isfinite(t0_shifts[j])) {
+        set_error("plan_create: t0 shift %d is not finite", j);
+        return ASHRT_EINVAL;
+      }
+  }
+  if (!(o.fmax_hz >= 0.f) || !(o.wavelet_peak_hz >= 0.f)) {
+    set_error("plan_create: fmax_hz and wavelet_peak_hz must be >= 0");
+    return ASHRT_EINVAL;
+  }
+
+  ashrt_plan* p = new ashrt_plan();
+  cudaGetDevice(&p->device);
+  p->nt = nt;
+  p->nx = nx;
+  p->nv = nv;
+  p->nt0 = nt0;
+  p->P = nv * nt0;
+  p->dt = dt;
+  p->dx = dx;
+  p->logNt = ilog2_ceil(o.pad_t * nt);
+  p->logNx = ilog2_ceil(o.pad_x * nx);
+  if (p->logNt < 6) p->logNt = 6;
+  if (p->logNx < 4) p->logNx = 4;
+  p->Nt = 1 << p->logNt;
+  p->Nx = 1 << p->logNx;
+  if (p->Nt > 4096 || p->Nx > 2048) {
+    set_error("plan_create: padded sizes Nt=%d, Nx=%d exceed 4096 / 2048", p->Nt, p->Nx);
+    delete p;
+    return ASHRT_EINVAL;
+  }
+  p->Lh = p->Nx / 2 + 1;
+  p->ld = (nt + 3) & ~3;
+  p->max_batch = o.max_batch;
+  p->with_solver = o.with_solver;
+  p->opts = o;
+
+  const int Nt = p->Nt, Nx = p->Nx, Lh = p->Lh;
+  // spectral weight W(w) / (Nt Nx): wavelet amplitude spectrum, band limit, no Nyquist
+  std::vector<float> wt(Nt);
+  for (int k = 0; k < Nt; ++k) {
+    const int kk = k <= Nt / 2 ? k : k - Nt;
+    const double f = std::fabs((double)kk) / (Nt * dt);
+    double w = 1.0;
+    if (o.wavelet_peak_hz > 0.f) {
+      const double z = (f / o.wavelet_peak_hz) * (f / o.wavelet_peak_hz);
+      w = z * std::exp(1.0 - z);
+    }
+    if (o.fmax_hz > 0.f && f > o.fmax_hz) w = 0.0;
+    if (k == Nt / 2) w = 0.0;
+    wt[k] = (float)(w / ((double)Nt * (double)Nx));
+  }
+  // cone: a = ((v*l)*Nt)*dt / (Nx*dx) in w-bin units; mapped iff k*k > a*a (FP64)
+  std::vector<int> kmin((size_t)nv * Lh);
+  std::vector<float2> acone((size_t)nv * Lh);
+  for (int i = 0; i < nv; ++i) {
+    const double v = (double)velocities[i];
+    for (int l = 0; l < Lh; ++l) {
+      const double a = ((v * (double)l) * (double)Nt) * dt / ((double)Nx * dx);
+      const double a2 = a * a;
+      long long k = Nt;   // a >= Nt: nothing of this row is mapped
+      if (a < (double)Nt) {
+        k = (long long)std::floor(a);
+        if (k < 0) k = 0;
+        while ((double)(k * k) <= a2) ++k;
+        while (k > 0 && (double)((k - 1) * (k - 1)) > a2) --k;
+      }
+      kmin[(size_t)i * Lh + l] = (int)std::min<long long>(k, Nt);
+      const float hi = (float)a;
+      acone[(size_t)i * Lh + l] = make_float2(hi, (float)(a - (double)hi));
+    }
+  }
+  // asymptote shift T: exp(-i w tau0), w = 2 pi kk / (Nt dt)
+  std::vector<float2> phase((size_t)nt0 * Nt);
+  bool shift = false;
+  for (int j = 0; j < nt0; ++j) {
+    const double t0 = t0_shifts ? (double)t0_shifts[j] : 0.0;
+    if (t0 != 0.0) shift = true;
+    for (int k = 0; k < Nt; ++k) {
+      const int kk = k <= Nt / 2 ? k : k - Nt;
+      const double ang = -2.0 * M_PI * (double)kk * t0 / ((double)Nt * dt);
+      phase[(size_t)j * Nt + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  }
+  p->shift = shift;
+  std::vector<float2> twt(twiddle_table_len(p->logNt)), twx(twiddle_table_len(p->logNx));
+  build_twiddle_table(p->logNt, twt.data());
+  build_twiddle_table(p->logNx, twx.data());
+
+  size_t total = 0;
+  ashrt_status st = ASHRT_OK;
+  auto chk = [&](ashrt_status s2) {
+    if (st == ASHRT_OK) st = s2;
+  };
+  chk(upload(&p->tw_t, twt, &total));
+  chk(upload(&p->tw_x, twx, &total));
+  chk(upload(&p->wt, wt, &total));
+  chk(upload(&p->kmin, kmin, &total));
+  chk(upload(&p->acone, acone, &total));
+  chk(upload(&p->phase, phase, &total));
+  const size_t B = (size_t)p->max_batch;
+  const size_t xpan = (size_t)Lh * p->ld;
+  if (st == ASHRT_OK) chk(dev_alloc(&p->X, B * p->P * xpan, &total));
+  if (st == ASHRT_OK) chk(dev_alloc(&p->Y, B * xpan, &total));
+  if (st == ASHRT_OK && p->with_solver) {
+    const size_t me = B * model_elems(p), de = B * data_elems(p);
+    chk(dev_alloc(&p->u, me, &total));
+    chk(dev_alloc(&p->pv, me, &total));
+    chk(dev_alloc(&p->sv, me, &total));
+    chk(dev_alloc(&p->wminv, me, &total));
+    chk(dev_alloc(&p->r, de, &total));
+    chk(dev_alloc(&p->qv, de, &total));
+    chk(dev_alloc(&p->wr, de, &total));
+    chk(dev_alloc(&p->y, de, &total));
+    chk(dev_alloc(&p->scal, B * kScalStride, &total));
+    chk(dev_alloc(&p->sel, B * kSelStride, &total));
+    chk(dev_alloc(&p->flags, 2 * B + 1, &total));
+  }
+  if (st == ASHRT_OK) {
+    // the padding columns of the spectra rows are never written: keep them zero
+    cudaError_t e = cudaMemset(p->X, 0, B * p->P * xpan * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemset(p->Y, 0, B * xpan * sizeof(float2));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_fail(e, "plan_create workspace init");
+  }
+  if (st != ASHRT_OK) {
+    free_plan_memory(p);
+    delete p;
+    return st;
+  }
+  p->ws_bytes = total;
+  *out = p;
+  return ASHRT_OK;
+}
+
+void ashrt_plan_destroy(ashrt_plan* p) {
+  if (!p) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  free_plan_memory(p);
+  cudaSetDevice(dev);
+  delete p;
+}
+
+ashrt_status ashrt_plan_info(const ashrt_plan* p, int* Nt, int* Nx, int* n_panels, size_t* ws) {
+  if (!p) {
+    set_error("plan_info: plan is NULL");
+    return ASHRT_EINVAL;
+  }
+  if (Nt) *Nt = p->Nt;
+  if (Nx) *Nx = p->Nx;
+  if (n_panels) *n_panels = p->P;
+  if (ws) *ws = p->ws_bytes;
+  return ASHRT_OK;
+}
+
+static ashrt_status check_call(const ashrt_plan* p, const void* a, const void* b, int batch,
+                               const char* who) {
+  g_err.clear();
+  if (!p || !a || !b) {
+    set_error("%s: NULL plan or array", who);
+    return ASHRT_EINVAL;
+  }
+  if (batch < 1 || batch > p->max_batch) {
+    set_error("%s: batch %d outside [1, max_batch = %d]", who, batch, p->max_batch);
+    return ASHRT_EINVAL;
+  }
+  return ASHRT_OK;
+}
+
+ashrt_status ashrt_forward(const ashrt_plan* p, const float* m, float* d, const float* tmask,
+                           int batch, void* stream) {
+  ashrt_status st = check_call(p, m, d, batch, "ashrt_forward");
+  if (st != ASHRT_OK) return st;
+  cudaError_t e = op_forward(p, m, d, nullptr, nullptr, tmask, nullptr, batch,
+                             (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ashrt_forward launch");
+  return ASHRT_OK;
+}
+
+ashrt_status ashrt_adjoint(const ashrt_plan* p, const float* d, float* m, const float* tmask,
+                           int batch, void* stream) {
+  ashrt_status st = check_call(p, d, m, batch, "ashrt_adjoint");
+  if (st != ASHRT_OK) return st;
+  cudaError_t e = op_adjoint(p, d, m, nullptr, nullptr, tmask, nullptr, batch,
+                             (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ashrt_adjoint launch");
+  return ASHRT_OK;
+}
+
+}  // extern "C"

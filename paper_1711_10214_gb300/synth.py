@@ -49,13 +49,21 @@ def draw_events(rng, n, nx, dx, tau_range, v_range, t0_range=None, amp=(1.0, 0.3
 
 
 def render(ev, nt, nx, dt, dx, f_peak):
-    """Sum of A * ricker(t - (t0 + sqrt(tau^2 + ((x - xa)/v)^2))) over events."""
-    t = np.arange(nt) * dt
+    """Sum of A * ricker(t - (t0 + sqrt(tau^2 + ((x - xa)/v)^2))) over events.
+
+    Each wavelet is evaluated within +-2/f_peak of its arrival, where the
+    Ricker envelope exp(-(pi f t)^2) has decayed below 1e-17."""
     x = np.arange(nx) * dx
     d = np.zeros((nx, nt))
+    half = int(np.ceil(2.0 / (f_peak * dt))) + 1
+    win = np.arange(-half, half + 1)
+    rows = np.arange(nx)[:, None]
     for tau, xa, v, A, t0 in zip(ev["tau"], ev["xa"], ev["v"], ev["A"], ev["t0"]):
         tx = t0 + np.sqrt(tau * tau + ((x - xa) / v) ** 2)
-        d += A * ricker(t[None, :] - tx[:, None], f_peak)
+        idx = np.rint(tx / dt).astype(np.int64)[:, None] + win[None, :]
+        ok = (idx >= 0) & (idx < nt)
+        vals = A * ricker(idx * dt - tx[:, None], f_peak)
+        np.add.at(d, (np.broadcast_to(rows, idx.shape)[ok], idx[ok]), vals[ok])
     return d
 
 

@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every function include/ashrt.h
+declares; host-side argument checks work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ashrt.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def cdll():
+    from paper_1711_10214_gb300 import ashrt, build
+    if not os.path.exists(ashrt.LIB_PATH):
+        build.build()
+    return ashrt.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ("ashrt_plan_create", "ashrt_forward", "ashrt_adjoint", "robust_irls_deblend",
+              "ashrt_plan_destroy", "ashrt_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(cdll):
+    for name in _declared_functions():
+        assert hasattr(cdll, name), name
+
+
+def test_host_side_calls_without_gpu(cdll):
+    from paper_1711_10214_gb300 import ashrt
+    o = ashrt.AshrtOpts()
+    cdll.ashrt_default_opts(ctypes.byref(o))
+    assert (o.pad_t, o.pad_x, o.max_batch, o.with_solver) == (2, 2, 1, 0)
+    io = ashrt.IrlsOpts()
+    cdll.irls_default_opts(ctypes.byref(io))
+    assert (io.p, io.q, io.n_outer, io.n_cg, io.b_r) == (1.0, 1.0, 5, 20, 1.345)
+    assert cdll.ashrt_status_string(4) == b"ASHRT_ENAN"
+    # argument errors are reported before any CUDA call
+    h = ctypes.c_void_p()
+    v = (ctypes.c_float * 1)(1500.0)
+    st = cdll.ashrt_plan_create(ctypes.byref(h), 1, 64, 0.004, 12.5, v, 1, None, 0, None, 1, None)
+    assert st == 1 and h.value is None
+    assert b"nt >= 2" in cdll.ashrt_last_error()
+    ax = (ctypes.c_float * 3)(0.0, 12.5, 30.0)     # apex grid must equal the trace grid
+    st = cdll.ashrt_plan_create(ctypes.byref(h), 64, 3, 0.004, 12.5, v, 1, ax, 3, None, 1, None)
+    assert st == 1 and b"x_a must equal x" in cdll.ashrt_last_error()
