@@ -41,6 +41,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="deblend", choices=["deblend", "ops"],
+                    help="ops: time forward+adjoint operator pairs only (profiling aid)")
+    ap.add_argument("--batch", type=int, default=B, help="gathers per call in --mode ops")
     return ap.parse_args()
 
 
@@ -290,8 +293,46 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ops(args):
+    """Operator pairs only, at the workload's gather size (not the bench line)."""
+    import numpy as np
+    import torch
+
+    from paper_1711_10214_gb300 import ashrt, synth
+    dev = torch.device("cuda", 0)
+    nb = args.batch
+    v = synth.velocity_scan(1400.0, 3500.0, NV)
+    plan = ashrt.Plan(NT, NX, DT, DX, v, wavelet_peak_hz=F_PEAK, max_batch=nb)
+    g = torch.Generator(device=dev).manual_seed(0)
+    m = torch.randn((nb,) + plan.model_shape, device=dev, generator=g)
+    d = torch.randn((nb, NX, NT), device=dev, generator=g)
+    for _ in range(args.warmup):
+        plan.forward(m, d, batch=nb)
+        plan.adjoint(d, m, batch=nb)
+    torch.cuda.synchronize()
+    ashrt.profile_read()
+    ashrt.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.forward(m, d, batch=nb)
+        plan.adjoint(d, m, batch=nb)
+    e1.record()
+    torch.cuda.synchronize()
+    ashrt.profile_enable(False)
+    prof = ashrt.profile_read()
+    t = e0.elapsed_time(e1) / 1000.0
+    print(json.dumps({"mode": "ops", "batch": nb, "pairs_per_s": nb * args.steps / t,
+                      "ms_per_pair_call": 1000.0 * t / args.steps,
+                      "kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items()}}),
+          flush=True)
+
+
 def main():
     args = _args()
+    if args.mode == "ops":
+        run_ops(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
