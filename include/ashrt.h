@@ -118,6 +118,35 @@ ashrt_status ashrt_forward(const ashrt_plan* plan, const float* m_dev, float* d_
 ashrt_status ashrt_adjoint(const ashrt_plan* plan, const float* d_dev, float* m_dev,
                            const float* trace_mask_dev, int batch, void* stream);
 
+/*
+ * Forward operator without a plan and without any device allocation.  The
+ * paper has no counterpart: this exists for callers that cannot allocate
+ * device memory -- a host application that owns the GPU's memory through its
+ * own allocator or a fixed budget and passes this library only its input and
+ * output buffers, or a latency-critical loop in which a cudaMalloc would
+ * synchronise the device.  Computes exactly what ashrt_forward computes for a
+ * plan with the same arguments (same kernels, same tables).
+ *   nt, nx, dt, dx, velocities/nv, t0_shifts/nt0, opts: as ashrt_plan_create
+ *     (apex positions are the trace positions; opts->max_batch and
+ *     opts->with_solver are ignored)
+ *   m_dev, d_dev, trace_mask_dev, batch, stream: as ashrt_forward
+ * Scratch: all tables and the operator workspace live in one static device
+ * array of 16 MiB that every GPU loading this library holds until the process
+ * exits.  A call whose tables plus workspace exceed it (roughly batch * nv *
+ * nt0 * (Nx/2 + 1) * nt * 8 bytes) returns ASHRT_EINVAL with the size it
+ * needed.  The call allocates nothing: no cudaMalloc, no cudaFree.
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture begins.  Every call rewrites the shared array (the tables are
+ * uploaded with cudaMemcpyAsync on `stream`), so calls that overlap on the GPU
+ * -- on different streams, or from different threads -- race: serialise them.
+ */
+ashrt_status ashrt_forward_static(int nt, int nx, double dt, double dx,
+                                  const float* velocities, int nv,
+                                  const float* t0_shifts, int nt0,
+                                  const ashrt_opts* opts, const float* m_dev, float* d_dev,
+                                  const float* trace_mask_dev, int batch, void* stream);
+
 /* Options of the robust solve (ch. 4). */
 typedef struct {
   double p;               /* misfit norm exponent, 0 < p <= 2 (1 = robust) */

@@ -78,6 +78,10 @@ def load():
     lib.robust_irls_deblend.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                                         P(IrlsOpts), P(IrlsReport), c_void_p]
     lib.robust_irls_deblend.restype = c_int
+    lib.ashrt_forward_static.argtypes = [c_int, c_int, c_double, c_double, P(c_float), c_int,
+                                         P(c_float), c_int, P(AshrtOpts), c_void_p, c_void_p,
+                                         c_void_p, c_int, c_void_p]
+    lib.ashrt_forward_static.restype = c_int
     lib.ashrt_last_error.argtypes = []
     lib.ashrt_last_error.restype = ctypes.c_char_p
     lib.ashrt_profile_enable.argtypes = [c_int]
@@ -142,6 +146,26 @@ def profile_read():
 
 def kernel_launches():
     return int(load().ashrt_kernel_launches())
+
+
+def forward_static(nt, nx, dt, dx, velocities, m, d, t0s=None, mask=None, batch=1, pad_t=2,
+                   pad_x=2, fmax_hz=0.0, wavelet_peak_hz=0.0, stream=None):
+    """ashrt_forward_static: the forward operator with no plan and no device
+    allocation (tables and workspace in the library's static scratch)."""
+    lib = load()
+    o = AshrtOpts()
+    lib.ashrt_default_opts(ctypes.byref(o))
+    o.pad_t, o.pad_x = int(pad_t), int(pad_x)
+    o.fmax_hz, o.wavelet_peak_hz = float(fmax_hz), float(wavelet_peak_hz)
+    va, vp = _farr(velocities)
+    if t0s is None:
+        tp, nt0 = None, 1
+    else:
+        ta, tp = _farr(t0s)
+        nt0 = ta.size
+    _check(lib.ashrt_forward_static(int(nt), int(nx), float(dt), float(dx), vp, va.size, tp,
+                                    nt0, ctypes.byref(o), _ptr(m), _ptr(d), _ptr(mask),
+                                    int(batch), _stream(stream)))
 
 
 class Plan:
