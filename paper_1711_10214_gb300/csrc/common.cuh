@@ -48,28 +48,64 @@ __device__ __forceinline__ float2 mul_3eighth(float2 a) {
                  : make_float2(-(a.x + a.y) * c, (a.x - a.y) * c);
 }
 
+// Two interleaved complex numbers (gather A in .x/.y, gather B in .z/.w): the
+// same operations applied to both halves, so one 16-byte shared-memory access
+// serves two rows and one twiddle serves both.
+__device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float4 pack2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ float4 cadd(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 csub(float4 a, float4 b) {
+  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 cmul(float4 a, float2 w) {
+  return make_float4(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x),
+                     fmaf(a.z, w.x, -a.w * w.y), fmaf(a.z, w.y, a.w * w.x));
+}
+__device__ __forceinline__ float4 cscale(float4 a, float s) {
+  return make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+}
+__device__ __forceinline__ float4 cfma(float s, float4 a, float4 acc) {
+  return make_float4(fmaf(s, a.x, acc.x), fmaf(s, a.y, acc.y), fmaf(s, a.z, acc.z),
+                     fmaf(s, a.w, acc.w));
+}
 template <int DIR>
-__device__ __forceinline__ void dft2(float2* v) {
-  float2 a = v[0], b = v[1];
+__device__ __forceinline__ float4 mul_quarter(float4 a) {
+  return DIR < 0 ? make_float4(a.y, -a.x, a.w, -a.z) : make_float4(-a.y, a.x, -a.w, a.z);
+}
+template <int DIR>
+__device__ __forceinline__ float4 mul_eighth(float4 a) {
+  return pack2(mul_eighth<DIR>(lo2(a)), mul_eighth<DIR>(hi2(a)));
+}
+template <int DIR>
+__device__ __forceinline__ float4 mul_3eighth(float4 a) {
+  return pack2(mul_3eighth<DIR>(lo2(a)), mul_3eighth<DIR>(hi2(a)));
+}
+
+template <int DIR, typename E>
+__device__ __forceinline__ void dft2(E* v) {
+  E a = v[0], b = v[1];
   v[0] = cadd(a, b);
   v[1] = csub(a, b);
 }
 
-template <int DIR>
-__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
-  float2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
-  float2 t3 = mul_quarter<DIR>(csub(v1, v3));
+template <int DIR, typename E>
+__device__ __forceinline__ void dft4(E& v0, E& v1, E& v2, E& v3) {
+  E t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
+  E t3 = mul_quarter<DIR>(csub(v1, v3));
   v0 = cadd(t0, t2);
   v2 = csub(t0, t2);
   v1 = cadd(t1, t3);
   v3 = csub(t1, t3);
 }
 
-template <int DIR>
-__device__ __forceinline__ void dft8(float2* v) {
+template <int DIR, typename E>
+__device__ __forceinline__ void dft8(E* v) {
   // even / odd split: X_q = E_q + w^q O_q, X_{q+4} = E_q - w^q O_q, w = exp(DIR i pi/4)
-  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  E e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  E o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
   dft4<DIR>(e0, e1, e2, e3);
   dft4<DIR>(o0, o1, o2, o3);
   o1 = mul_eighth<DIR>(o1);
@@ -81,16 +117,16 @@ __device__ __forceinline__ void dft8(float2* v) {
   v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
 }
 
-template <int DIR, int R>
-__device__ __forceinline__ void dft_r(float2* v) {
+template <int DIR, int R, typename E>
+__device__ __forceinline__ void dft_r(E* v) {
   if constexpr (R == 2) dft2<DIR>(v);
   else if constexpr (R == 4) dft4<DIR>(v[0], v[1], v[2], v[3]);
   else dft8<DIR>(v);
 }
 
 // v[r] *= w^r, r = 1..R-1 (w already carries the direction).
-template <int R>
-__device__ __forceinline__ void twiddle_r(float2* v, float2 w) {
+template <int R, typename E>
+__device__ __forceinline__ void twiddle_r(E* v, float2 w) {
   if constexpr (R == 2) {
     v[1] = cmul(v[1], w);
   } else if constexpr (R == 4) {
@@ -133,10 +169,17 @@ struct Sched {
   static constexpr int TW_LEN = tw_off(NPASS);
 };
 
-// Shared-memory swizzle for length-N rows of float2: XOR the low four index
-// bits with the next four, which spreads the strided Stockham writes over
-// the banks.  A bijection on [0, N) for N a multiple of 16 (identity below).
+// Shared-memory swizzles for one length-N row: XOR the column bits of a
+// 128-byte bank row with the next bits of the index, which spreads the
+// strided Stockham writes over all banks.  float2 rows: 16 elements per bank
+// row; float4 rows (two interleaved complex rows): 8.  Bijections on [0, N).
 __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 4) & 15); }
+__device__ __forceinline__ int swz4(int i) { return i ^ ((i >> 3) & 7); }
+template <typename E>
+__device__ __forceinline__ int swz_e(int i) {
+  if constexpr (sizeof(E) == 16) return swz4(i);
+  else return swz(i);
+}
 
 // Base twiddle of pass q: exp(DIR 2 pi i k / (Ns R)) read from the per-length
 // table (stored for DIR = -1; conjugated for the synthesis direction).
@@ -151,17 +194,17 @@ __device__ __forceinline__ float2 base_twiddle(const float2* __restrict__ tw, in
 // One in-place Stockham pass on a single shared row of N float2, executed by
 // T = N/8 threads (each handles 8 values: one radix-8, two radix-4 or four
 // radix-2 butterflies).  Reads everything, barrier, writes, barrier.
-template <int DIR, int N, int R>
-__device__ __forceinline__ void row_pass(float2* buf, int Ns, const float2* __restrict__ tw,
+template <int DIR, int N, int R, typename E>
+__device__ __forceinline__ void row_pass(E* buf, int Ns, const float2* __restrict__ tw,
                                          int tw_off, int tid) {
   constexpr int T = N / 8;
   constexpr int NB = 8 / R;
-  float2 v[8];
+  E v[8];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz(jb + r * (N / R))];
+    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz_e<E>(jb + r * (N / R))];
   }
   __syncthreads();
 #pragma unroll
@@ -172,41 +215,50 @@ __device__ __forceinline__ void row_pass(float2* buf, int Ns, const float2* __re
     dft_r<DIR, R>(&v[q * R]);
     const int base = (jb - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[swz(base + r * Ns)] = v[q * R + r];
+    for (int r = 0; r < R; ++r) buf[swz_e<E>(base + r * Ns)] = v[q * R + r];
   }
   __syncthreads();
 }
 
 // Passes Q0 <= q < Q1 of a length-2^LOGN transform, in place in shared memory.
-template <int DIR, int LOGN, int Q0, int Q1>
-__device__ __forceinline__ void row_pass_range(float2* buf, const float2* __restrict__ tw,
+template <int DIR, int LOGN, int Q0, int Q1, typename E>
+__device__ __forceinline__ void row_pass_range(E* buf, const float2* __restrict__ tw,
                                                int tid) {
   using S = Sched<LOGN>;
   if constexpr (Q0 < Q1) {
     constexpr int R = S::radix(Q0);
-    row_pass<DIR, S::N, R>(buf, S::ns(Q0), tw, S::tw_off(Q0), tid);
+    row_pass<DIR, S::N, R, E>(buf, S::ns(Q0), tw, S::tw_off(Q0), tid);
     row_pass_range<DIR, LOGN, Q0 + 1, Q1>(buf, tw, tid);
   }
 }
 
 // Last pass of a length-2^LOGN transform, read from shared memory and written
-// to a global row, keeping outputs with index < n_keep (the crop back to nt).
+// to global rows, keeping outputs with index < n_keep (the crop back to nt).
 // In the last pass Ns = N/R > jb, so output r of butterfly jb lands at
-// jb + r Ns: consecutive threads store consecutive addresses.
-template <int DIR, int LOGN>
-__device__ __forceinline__ void row_last_pass_global(float2* buf, const float2* __restrict__ tw,
-                                                     int tid, float2* __restrict__ out,
-                                                     int n_keep) {
+// jb + r Ns: consecutive threads store consecutive addresses.  For float4
+// elements the two interleaved rows go to outA and outB (outB may be null).
+__device__ __forceinline__ void store_out(float2* outA, float2* outB, int idx, float2 v) {
+  outA[idx] = v;
+}
+__device__ __forceinline__ void store_out(float2* outA, float2* outB, int idx, float4 v) {
+  outA[idx] = lo2(v);
+  if (outB) outB[idx] = hi2(v);
+}
+
+template <int DIR, int LOGN, typename E>
+__device__ __forceinline__ void row_last_pass_global(E* buf, const float2* __restrict__ tw,
+                                                     int tid, float2* __restrict__ outA,
+                                                     float2* __restrict__ outB, int n_keep) {
   using S = Sched<LOGN>;
   constexpr int Q = S::NPASS - 1;
   constexpr int R = S::radix(Q);
   constexpr int N = S::N, T = N / 8, NB = 8 / R, Ns = S::ns(Q);
-  float2 v[8];
+  E v[8];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz(jb + r * (N / R))];
+    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz_e<E>(jb + r * (N / R))];
   }
   __syncthreads();
 #pragma unroll
@@ -217,17 +269,17 @@ __device__ __forceinline__ void row_last_pass_global(float2* buf, const float2* 
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int idx = jb + r * Ns;
-      if (idx < n_keep) out[idx] = v[q * R + r];
+      if (idx < n_keep) store_out(outA, outB, idx, v[q * R + r]);
     }
   }
 }
 
 // First pass (radix 8, Ns = 1, no twiddles) from registers v[r] = x[tid + r N/8].
-template <int DIR, int N>
-__device__ __forceinline__ void row_first_pass(float2* buf, float2* v, int tid) {
+template <int DIR, int N, typename E>
+__device__ __forceinline__ void row_first_pass(E* buf, E* v, int tid) {
   dft8<DIR>(v);
 #pragma unroll
-  for (int r = 0; r < 8; ++r) buf[swz(tid * 8 + r)] = v[r];
+  for (int r = 0; r < 8; ++r) buf[swz_e<E>(tid * 8 + r)] = v[r];
   __syncthreads();
 }
 

@@ -1,5 +1,5 @@
 // Fused time-axis FFT + Stolt map + velocity/asymptote sum (forward) or
-// spray (adjoint), one CTA per (gather, k_x) row.
+// spray (adjoint), one CTA per (gather pair, k_x) row.
 //
 // Forward, ch. 5 Eq. ch5_forward_operator / ch. 6 Eq. ch6_forward_operator,
 // for the row of wavenumber index l of gather b:
@@ -14,10 +14,13 @@
 // scatter every mapped bin to its two interpolation taps (transposed linear
 // weights, conjugate phase), inverse FFT, keep nt samples.
 //
-// The panel spectrum, the map and the accumulation never leave the SM: the
-// accumulator D lives in registers (each thread owns bins k = tid + T s), the
-// spectrum of the current panel in one shared row, and the next panel's row
-// is prefetched into registers while the current one is transformed.
+// One CTA handles one k_x row of a PAIR of gathers, the two rows interleaved
+// element by element (16-byte shared accesses; twiddles and Stolt taps
+// computed once for both).  The panel spectrum, the map and the accumulation
+// never leave the SM: the accumulator D lives in registers (each thread owns
+// bins k = tid + T s), the spectrum of the current panel in one shared row,
+// and the next panel's rows are staged with cp.async while the current one
+// is transformed.
 //
 // Cone membership (k^2 > a^2, strict; never the w-Nyquist bin) comes from
 // the host's FP64 table kmin[v][l], so the GPU and the FP64 oracle agree on
@@ -67,36 +70,85 @@ __device__ __forceinline__ Tap stolt_tap(int k, int kmin, float2 ac) {
   return t;
 }
 
+// 16-byte asynchronous global -> shared copies (Ampere-style cp.async; no
+// waits beyond cp.async.wait_group, which the hardware completes).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// Stage the rows of gathers A and B (B may be absent) of one panel: ld
+// complex values each (ld is a multiple of 4, rows are 32-byte aligned).
+__device__ __forceinline__ void stage_rows(float2* stage, const float2* rowA, const float2* rowB,
+                                           int ld, int tid, int T) {
+  const int chunks = ld >> 1;   // 16-byte chunks of two complex values
+  for (int c = tid; c < chunks; c += T) cp_async16(stage + 2 * c, rowA + 2 * c);
+  if (rowB)
+    for (int c = tid; c < chunks; c += T) cp_async16(stage + ld + 2 * c, rowB + 2 * c);
+  cp_async_commit();
+}
+
 template <int N>
-__device__ __forceinline__ void load_row(float2* v, const float2* __restrict__ row, int nt, int tid) {
+__device__ __forceinline__ void load_pair(float4* v, const float2* __restrict__ rowA,
+                                          const float2* __restrict__ rowB, int nt, int tid) {
   constexpr int T = N / 8;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int i = tid + r * T;
-    v[r] = i < nt ? __ldg(row + i) : make_float2(0.f, 0.f);
+    const float2 za = i < nt ? __ldg(rowA + i) : make_float2(0.f, 0.f);
+    const float2 zb = (rowB && i < nt) ? __ldg(rowB + i) : make_float2(0.f, 0.f);
+    v[r] = pack2(za, zb);
   }
 }
 
-template <int LOGN, bool SHIFT>
-__global__ void __launch_bounds__((1 << LOGN) / 8)
+// Forward rows.  CTA = (k_x row l, pair of gathers b0, b0+1): the two rows
+// are interleaved element by element, so every shared access is 16 bytes and
+// the twiddles and Stolt taps are computed once for both gathers.
+template <int LOGN, bool SHIFT, int MINB>
+__global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
 stolt_fwd_rows(RowArgs a) {
   constexpr int N = 1 << LOGN, T = N / 8;
   using S = Sched<LOGN>;
-  __shared__ float2 buf[N];
-  const int tid = threadIdx.x, l = blockIdx.x, b = blockIdx.y;
-  const float2* xrow = a.X + (long long)b * a.x_batch + (long long)l * a.ld;
+  extern __shared__ float4 smem4[];
+  float4* buf = smem4;                         // N interleaved (A, B) complex values
+  float2* stage = (float2*)(smem4 + N);        // next panel: row A [ld], row B [ld]
+  const int tid = threadIdx.x, l = blockIdx.x, b0 = 2 * blockIdx.y;
+  const bool hasB = b0 + 1 < a.batch;
+  const float2* xA = a.X + (long long)b0 * a.x_batch + (long long)l * a.ld;
+  const float2* xB = hasB ? xA + a.x_batch : nullptr;
 
-  float2 acc[8], accj[8], pf[8];
+  float4 acc[8];
+  float2 ph[8];
 #pragma unroll
-  for (int s = 0; s < 8; ++s) acc[s] = accj[s] = make_float2(0.f, 0.f);
-  load_row<N>(pf, xrow, a.nt, tid);
+  for (int s = 0; s < 8; ++s) {
+    acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    ph[s] = make_float2(1.f, 0.f);
+  }
+  stage_rows(stage, xA, xB, a.ld, tid, T);
 
   int iv = 0, jt = 0;
   for (int p = 0; p < a.P; ++p) {
-    float2 v[8];
+    cp_async_wait_all();
+    __syncthreads();
+    float4 v[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = pf[r];
-    if (p + 1 < a.P) load_row<N>(pf, xrow + (long long)(p + 1) * a.x_panel, a.nt, tid);
+    for (int r = 0; r < 8; ++r) {
+      const int i = tid + r * T;
+      const float2 za = i < a.nt ? stage[i] : make_float2(0.f, 0.f);
+      const float2 zb = (hasB && i < a.nt) ? stage[a.ld + i] : make_float2(0.f, 0.f);
+      v[r] = pack2(za, zb);
+    }
+    __syncthreads();
+    if (p + 1 < a.P) {
+      const long long o = (long long)(p + 1) * a.x_panel;
+      stage_rows(stage, xA + o, hasB ? xB + o : nullptr, a.ld, tid, T);
+    }
+    if (SHIFT && iv == 0) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) ph[s] = __ldg(a.phase + (long long)jt * N + tid + T * s);
+    }
     row_first_pass<-1, N>(buf, v, tid);
     row_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw, tid);
 
@@ -104,24 +156,15 @@ stolt_fwd_rows(RowArgs a) {
     const float2 ac = __ldg(a.acone + iv * a.Lh + l);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      const int k = tid + T * s;
-      const Tap t = stolt_tap<N>(k, km, ac);
+      const Tap t = stolt_tap<N>(tid + T * s, km, ac);
       if (t.valid) {
-        float2 vk = cscale(buf[swz(t.i0)], t.w0);
-        vk = cfma(t.w1, buf[swz(t.i1)], vk);
-        if (SHIFT) accj[s] = cadd(accj[s], vk);
-        else acc[s] = cadd(acc[s], vk);
+        float4 vk = cscale(buf[swz4(t.i0)], t.w0);
+        vk = cfma(t.w1, buf[swz4(t.i1)], vk);
+        if (SHIFT) vk = cmul(vk, ph[s]);
+        acc[s] = cadd(acc[s], vk);
       }
     }
     if (++iv == a.nv) {
-      if (SHIFT) {
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const int k = tid + T * s;
-          acc[s] = cadd(acc[s], cmul(__ldg(a.phase + (long long)jt * N + k), accj[s]));
-          accj[s] = make_float2(0.f, 0.f);
-        }
-      }
       iv = 0;
       ++jt;
     }
@@ -132,64 +175,129 @@ stolt_fwd_rows(RowArgs a) {
   // own bins are exactly the first-pass inputs of the inverse transform
   row_first_pass<+1, N>(buf, acc, tid);
   row_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw, tid);
-  float2* yrow = a.Yw + (long long)b * a.y_batch + (long long)l * a.ld;
-  row_last_pass_global<+1, LOGN>(buf, a.tw, tid, yrow, a.nt);
+  float2* yA = a.Yw + (long long)b0 * a.y_batch + (long long)l * a.ld;
+  row_last_pass_global<+1, LOGN>(buf, a.tw, tid, yA, hasB ? yA + a.y_batch : nullptr, a.nt);
 }
 
-template <int LOGN, bool SHIFT>
-__global__ void __launch_bounds__((1 << LOGN) / 8)
+// Adds (atomic) or stores (exclusive) one merged contribution of the
+// adjoint scatter.  The w-Nyquist target only ever receives zero weight.
+__device__ __forceinline__ void scatter_flush(float4* buf, int target, float4 v, bool atomic,
+                                              bool hasB, int N) {
+  const int t = target & (N - 1);
+  if (t == (N >> 1)) return;
+  float4* q = &buf[swz4(t)];
+  if (!atomic) {
+    *q = v;
+    return;
+  }
+  float* f = (float*)q;
+  atomicAdd(f + 0, v.x);
+  atomicAdd(f + 1, v.y);
+  if (hasB) {
+    atomicAdd(f + 2, v.z);
+    atomicAdd(f + 3, v.w);
+  }
+}
+
+// Adjoint rows: the exact transpose.  The data rows of the gather pair are
+// transformed once.  For every panel each mapped source bin k sends its
+// weighted value to its two interpolation taps.  The fractional index u(k)
+// (FP32, monotone in |k|) makes the taps of ascending sources ascend, so each
+// thread owns 8 contiguous source bins, merges the contributions of its
+// sources to equal targets in registers, and writes its targets in order:
+// targets only it touches with plain stores, the first two and last two
+// (which a neighbouring thread may share) with shared-memory atomics.
+template <int LOGN, bool SHIFT, int MINB>
+__global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
 stolt_adj_rows(RowArgs a) {
   constexpr int N = 1 << LOGN, T = N / 8;
   using S = Sched<LOGN>;
-  __shared__ float2 buf[N];
-  const int tid = threadIdx.x, l = blockIdx.x, b = blockIdx.y;
-  const float2* yrow = a.Y + (long long)b * a.y_batch + (long long)l * a.ld;
+  extern __shared__ float4 smem4[];
+  float4* buf = smem4;
+  const int tid = threadIdx.x, l = blockIdx.x, b0 = 2 * blockIdx.y;
+  const bool hasB = b0 + 1 < a.batch;
+  const float2* yA = a.Y + (long long)b0 * a.y_batch + (long long)l * a.ld;
 
-  float2 v[8];
-  load_row<N>(v, yrow, a.nt, tid);
+  float4 v[8];
+  load_pair<N>(v, yA, hasB ? yA + a.y_batch : nullptr, a.nt, tid);
   row_first_pass<-1, N>(buf, v, tid);
   row_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw, tid);
-  float2 ds[8], dj[8];
+  // own sources: the contiguous bins k = 8 tid + s
+  float4 ds[8];
+  float2 ph[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
-    const int k = tid + T * s;
-    ds[s] = cscale(buf[swz(k)], __ldg(a.wt + k));
-    dj[s] = ds[s];
+    const int k = 8 * tid + s;
+    ds[s] = cscale(buf[swz4(k)], __ldg(a.wt + k));
+    ph[s] = make_float2(1.f, 0.f);
   }
   __syncthreads();
 
-  float2* xrow = a.Xw + (long long)b * a.x_batch + (long long)l * a.ld;
+  float2* xA = a.Xw + (long long)b0 * a.x_batch + (long long)l * a.ld;
+  float2* xB = hasB ? xA + a.x_batch : nullptr;
   int iv = 0, jt = 0;
   for (int p = 0; p < a.P; ++p) {
     if (SHIFT && iv == 0) {
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const int k = tid + T * s;
-        dj[s] = cmul(ds[s], cconj(__ldg(a.phase + (long long)jt * N + k)));
-      }
+      for (int s = 0; s < 8; ++s) ph[s] = cconj(__ldg(a.phase + (long long)jt * N + 8 * tid + s));
     }
 #pragma unroll
-    for (int s = 0; s < 8; ++s) buf[swz(tid + T * s)] = make_float2(0.f, 0.f);
+    for (int s = 0; s < 8; ++s) buf[swz4(tid + T * s)] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const int km = __ldg(a.kmin + iv * a.Lh + l);
     const float2 ac = __ldg(a.acone + iv * a.Lh + l);
+    // running window over the two consecutive targets (cur, cur + 1)
+    int cur = -1, nflush = 0;
+    float4 A0 = make_float4(0.f, 0.f, 0.f, 0.f), A1 = A0;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      const Tap t = stolt_tap<N>(tid + T * s, km, ac);
-      if (t.valid) {
-        float2* p0 = &buf[swz(t.i0)];
-        atomicAdd(&p0->x, t.w0 * dj[s].x);
-        atomicAdd(&p0->y, t.w0 * dj[s].y);
-        if (t.w1 != 0.f) {
-          float2* p1 = &buf[swz(t.i1)];
-          atomicAdd(&p1->x, t.w1 * dj[s].x);
-          atomicAdd(&p1->y, t.w1 * dj[s].y);
-        }
+      const int k = 8 * tid + s;
+      const Tap t = stolt_tap<N>(k, km, ac);
+      if (!t.valid) continue;
+      // targets (base, base + 1) in unwrapped natural order with their weights
+      int base;
+      float wl, wh;
+      if (k < N / 2) {
+        base = t.i0;
+        wl = t.w0;
+        wh = t.w1;
+      } else {
+        base = t.i0 == 0 ? N - 1 : t.i0 - 1;   // = N - floor(u) - 1
+        wl = t.w1;
+        wh = t.w0;
       }
+      const float4 c = SHIFT ? cmul(ds[s], ph[s]) : ds[s];
+      if (cur < 0) {
+        cur = base;
+        A0 = cscale(c, wl);
+        A1 = cscale(c, wh);
+      } else if (base == cur) {
+        A0 = cfma(wl, c, A0);
+        A1 = cfma(wh, c, A1);
+      } else if (base == cur + 1) {
+        scatter_flush(buf, cur, A0, nflush < 2, hasB, N);
+        ++nflush;
+        cur = base;
+        A0 = cfma(wl, c, A1);
+        A1 = cscale(c, wh);
+      } else {
+        scatter_flush(buf, cur, A0, nflush < 2, hasB, N);
+        ++nflush;
+        scatter_flush(buf, cur + 1, A1, nflush < 2, hasB, N);
+        ++nflush;
+        cur = base;
+        A0 = cscale(c, wl);
+        A1 = cscale(c, wh);
+      }
+    }
+    if (cur >= 0) {
+      scatter_flush(buf, cur, A0, true, hasB, N);
+      scatter_flush(buf, cur + 1, A1, true, hasB, N);
     }
     __syncthreads();
     row_pass_range<+1, LOGN, 0, S::NPASS - 1>(buf, a.tw, tid);
-    row_last_pass_global<+1, LOGN>(buf, a.tw, tid, xrow + (long long)p * a.x_panel, a.nt);
+    const long long o = (long long)p * a.x_panel;
+    row_last_pass_global<+1, LOGN>(buf, a.tw, tid, xA + o, hasB ? xB + o : nullptr, a.nt);
     if (++iv == a.nv) {
       iv = 0;
       ++jt;
@@ -197,20 +305,53 @@ stolt_adj_rows(RowArgs a) {
   }
 }
 
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes, bool& done) {
+  if (done || bytes <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+// Resident CTAs per SM the row kernels are compiled for: up to Nt = 2048 the
+// register cap of 3 CTAs (80 registers) measured 1.4x (forward) and 1.9x
+// (adjoint) faster than the uncapped build; Nt = 4096 CTAs have 512 threads.
 template <int LOGN>
-cudaError_t launch_fwd_t(const RowArgs& a, cudaStream_t s) {
-  dim3 grid(a.Lh, a.batch);
-  if (a.phase) stolt_fwd_rows<LOGN, true><<<grid, (1 << LOGN) / 8, 0, s>>>(a);
-  else stolt_fwd_rows<LOGN, false><<<grid, (1 << LOGN) / 8, 0, s>>>(a);
+__host__ __device__ constexpr int rows_minb() { return LOGN <= 11 ? 3 : 1; }
+
+template <int LOGN, bool SHIFT, int MINB>
+cudaError_t launch_fwd_v(const RowArgs& a, cudaStream_t s) {
+  constexpr int N = 1 << LOGN;
+  static bool attr = false;
+  const size_t smem = (size_t)N * sizeof(float4) + (size_t)2 * N * sizeof(float2);   // ld <= N
+  cudaError_t e = set_smem(stolt_fwd_rows<LOGN, SHIFT, MINB>, smem, attr);
+  if (e != cudaSuccess) return e;
+  stolt_fwd_rows<LOGN, SHIFT, MINB><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LOGN, bool SHIFT, int MINB>
+cudaError_t launch_adj_v(const RowArgs& a, cudaStream_t s) {
+  constexpr int N = 1 << LOGN;
+  static bool attr = false;
+  const size_t smem = (size_t)N * sizeof(float4);
+  cudaError_t e = set_smem(stolt_adj_rows<LOGN, SHIFT, MINB>, smem, attr);
+  if (e != cudaSuccess) return e;
+  stolt_adj_rows<LOGN, SHIFT, MINB><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int LOGN>
+cudaError_t launch_fwd_t(const RowArgs& a, cudaStream_t s) {
+  constexpr int M = rows_minb<LOGN>();
+  return a.phase ? launch_fwd_v<LOGN, true, M>(a, s) : launch_fwd_v<LOGN, false, M>(a, s);
+}
+
+template <int LOGN>
 cudaError_t launch_adj_t(const RowArgs& a, cudaStream_t s) {
-  dim3 grid(a.Lh, a.batch);
-  if (a.phase) stolt_adj_rows<LOGN, true><<<grid, (1 << LOGN) / 8, 0, s>>>(a);
-  else stolt_adj_rows<LOGN, false><<<grid, (1 << LOGN) / 8, 0, s>>>(a);
-  return cudaGetLastError();
+  constexpr int M = rows_minb<LOGN>();
+  return a.phase ? launch_adj_v<LOGN, true, M>(a, s) : launch_adj_v<LOGN, false, M>(a, s);
 }
 
 int row_log2(int n) {

@@ -6,10 +6,10 @@
 //   c2r: a Hermitian half spectrum [Lh][nt] -> the real panel, synthesis
 //        exp(+i k_x x), unnormalised, cropped to nx traces.
 //
-// One CTA transforms 2*C consecutive time columns of one panel: columns
-// t0 + c and t0 + C + c are packed as the real and imaginary parts of one
-// complex sequence, transformed together, and separated with the Hermitian
-// symmetry of real signals.  The length-Nx transforms run as Stockham passes
+// One CTA transforms 2*C consecutive time columns of one panel: adjacent
+// columns t, t+1 are packed as the real and imaginary parts of one complex
+// sequence (one 8-byte load per trace), transformed together, and separated
+// with the Hermitian symmetry of real signals (one 16-byte store per row).  The length-Nx transforms run as Stockham passes
 // over a shared [Nx][C] tile; the first pass is fed straight from global
 // memory and (c2r) the last pass stores straight to global memory.  The
 // per-element weights of the IRLS operator (W_m^-1 on the model side,
@@ -24,8 +24,6 @@
 namespace ashrt {
 
 namespace {
-
-constexpr int kCols = 8;   // complex columns per CTA (16 real time samples)
 
 template <int DIR, int N, int C, int R>
 __device__ __forceinline__ void col_pass(float2* sm, int Ns, const float2* __restrict__ tw,
@@ -83,141 +81,182 @@ __device__ __forceinline__ void block_accumulate(double part, double* dst) {
   }
 }
 
+// Complex columns per CTA: 16 (32 real time samples = one 128-byte line per
+// trace) up to Nx = 512, 8 beyond so a CTA stays within 1024 threads / 64 KB.
 template <int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) * kCols / 16)
+__host__ __device__ constexpr int cols_for() { return LOGN <= 9 ? 16 : 8; }
+
+// Real time samples t and t+1 of one trace, packed as z = x_t + i x_{t+1}
+// (one 8-byte load when the row is 8-byte aligned).
+__device__ __forceinline__ float2 load_pair_real(const float* __restrict__ row, int t, int nt,
+                                                 bool vec) {
+  if (vec && t + 1 < nt) return __ldg((const float2*)(row + t));
+  return make_float2(t < nt ? __ldg(row + t) : 0.f, t + 1 < nt ? __ldg(row + t + 1) : 0.f);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) * cols_for<LOGN>() / 16)
 xfft_r2c_kernel(XfftArgs a) {
-  constexpr int N = 1 << LOGN, C = kCols, T = N * C / 16, JS = T / C;
+  constexpr int N = 1 << LOGN, C = cols_for<LOGN>(), T = N * C / 16, JS = T / C;
   using S = Sched<LOGN>;
   extern __shared__ float2 sm[];   // [N][C]
   const int tid = threadIdx.x, col = tid % C, j0 = tid / C;
   const long long slab = blockIdx.x;
   const int t0 = blockIdx.y * 2 * C;
-  const int ta = t0 + col, tb = t0 + C + col;
-  const bool oka = ta < a.nt, okb = tb < a.nt;
+  const int ta = t0 + 2 * col;      // this thread packs columns ta (real) and ta + 1 (imag)
+  const bool vec = (a.nt & 1) == 0;
   const float* in = a.in_real + slab * a.slab_real;
   const float* ew = a.ew ? a.ew + slab * a.slab_real : nullptr;
   const float* tm = a.tmask ? a.tmask + (slab / a.slabs_per_gather) * a.nx : nullptr;
 
-  // first pass (radix 8, Ns = 1): inputs at rows jb + r N/8; rows >= nx are the zero padding
+  // first pass (radix 8, Ns = 1) for both butterflies of this thread: all
+  // loads first; rows >= nx are the zero padding
+  float2 v[2][8];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int jb = j0 + JS * q;
-    float2 v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int row = jb + r * (N / 8);
-      float xa = 0.f, xb = 0.f;
+      float2 z = make_float2(0.f, 0.f);
       if (row < a.nx) {
         const long long o = (long long)row * a.nt;
-        float wa = 1.f, wb = 1.f;
-        if (ew) { wa = oka ? __ldg(ew + o + ta) : 0.f; wb = okb ? __ldg(ew + o + tb) : 0.f; }
-        const float g = tm ? __ldg(tm + row) : 1.f;
-        xa = oka ? __ldg(in + o + ta) * wa * g : 0.f;
-        xb = okb ? __ldg(in + o + tb) * wb * g : 0.f;
+        z = load_pair_real(in + o, ta, a.nt, vec);
+        if (ew) {
+          const float2 w = load_pair_real(ew + o, ta, a.nt, vec);
+          z.x *= w.x;
+          z.y *= w.y;
+        }
+        if (tm) {
+          const float g = __ldg(tm + row);
+          z.x *= g;
+          z.y *= g;
+        }
       }
-      v[r] = make_float2(xa, xb);
+      v[q][r] = z;
     }
-    dft8<-1>(v);
+  }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) sm[(jb * 8 + r) * C + col] = v[r];
+  for (int q = 0; q < 2; ++q) {
+    const int jb = j0 + JS * q;
+    dft8<-1>(v[q]);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sm[(jb * 8 + r) * C + col] = v[q][r];
   }
   __syncthreads();
   col_pass_range<-1, LOGN, C, 1, S::NPASS>(sm, a.tw, tid);
 
-  // separate the two packed real columns: A = (Z_l + conj Z_{N-l}) / 2,
-  // B = (Z_l - conj Z_{N-l}) / (2i), for 0 <= l <= N/2
+  // separate the packed columns: A = (Z_l + conj Z_{N-l}) / 2 (column ta),
+  // B = (Z_l - conj Z_{N-l}) / (2i) (column ta + 1), 0 <= l <= N/2; one
+  // 16-byte store of (A, B) per row
   float2* out = a.out_cplx + slab * a.slab_cplx;
   for (int f = tid; f < (N / 2 + 1) * C; f += T) {
     const int l = f / C, c = f % C;
     const float2 zl = sm[l * C + c];
     const float2 zm = sm[((N - l) & (N - 1)) * C + c];
-    const float2 A = make_float2(0.5f * (zl.x + zm.x), 0.5f * (zl.y - zm.y));
-    const float2 B = make_float2(0.5f * (zl.y + zm.y), -0.5f * (zl.x - zm.x));
-    if (t0 + c < a.nt) out[(long long)l * a.ld + t0 + c] = A;
-    if (t0 + C + c < a.nt) out[(long long)l * a.ld + t0 + C + c] = B;
+    const float4 AB = make_float4(0.5f * (zl.x + zm.x), 0.5f * (zl.y - zm.y),
+                                  0.5f * (zl.y + zm.y), -0.5f * (zl.x - zm.x));
+    const int t = t0 + 2 * c;
+    float2* o = out + (long long)l * a.ld + t;
+    if (t + 1 < a.nt) {
+      *(float4*)o = AB;
+    } else if (t < a.nt) {
+      o[0] = make_float2(AB.x, AB.y);
+    }
   }
 }
 
-// Hermitian extension of a stored half spectrum: row l of the full length-N
-// spectrum; rows 0 and N/2 keep their real parts only (real signal).
+// Hermitian extension of a stored half spectrum for two adjacent columns at
+// once: row l of the full length-N spectrum; rows 0 and N/2 keep their real
+// parts only (real signal).  Returns (A, B) of columns t and t+1 (t even).
+// Rows are ld >= nt long with ld a multiple of 4, so the 16-byte load at an
+// even t < nt stays inside the row; column t+1 >= nt is zeroed afterwards.
 template <int N>
-__device__ __forceinline__ float2 herm_load(const float2* __restrict__ base, int ld, int row, int t,
-                                            bool ok) {
-  if (!ok) return make_float2(0.f, 0.f);
-  if (row == 0 || row == N / 2) {
-    float2 y = __ldg(base + (long long)row * ld + t);
-    return make_float2(y.x, 0.f);
-  }
-  if (row < N / 2) return __ldg(base + (long long)row * ld + t);
-  float2 y = __ldg(base + (long long)(N - row) * ld + t);
-  return make_float2(y.x, -y.y);
+__device__ __forceinline__ float4 herm_load2(const float2* __restrict__ base, int ld, int row, int t,
+                                             int nt) {
+  const bool ok = t < nt;
+  const int r = row <= N / 2 ? row : N - row;
+  float4 y = __ldg((const float4*)(base + (long long)r * ld + (ok ? t : 0)));
+  const float sy = (row == 0 || row == N / 2) ? 0.f : (row > N / 2 ? -1.f : 1.f);
+  const bool okb = t + 1 < nt;
+  return make_float4(ok ? y.x : 0.f, ok ? y.y * sy : 0.f, okb ? y.z : 0.f, okb ? y.w * sy : 0.f);
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) * kCols / 16)
+__global__ void __launch_bounds__((1 << LOGN) * cols_for<LOGN>() / 16)
 xfft_c2r_kernel(XfftArgs a) {
-  constexpr int N = 1 << LOGN, C = kCols, T = N * C / 16, JS = T / C;
+  constexpr int N = 1 << LOGN, C = cols_for<LOGN>(), T = N * C / 16, JS = T / C;
   using S = Sched<LOGN>;
   extern __shared__ float2 sm[];   // [N][C]
   const int tid = threadIdx.x, col = tid % C, j0 = tid / C;
   const long long slab = blockIdx.x;
   const int t0 = blockIdx.y * 2 * C;
-  const int ta = t0 + col, tb = t0 + C + col;
-  const bool oka = ta < a.nt, okb = tb < a.nt;
+  const int ta = t0 + 2 * col;
   const float2* in = a.in_cplx + slab * a.slab_cplx;
 
-  // first pass: Z = A + i B with A, B the Hermitian-extended spectra of the two columns
+  // first pass: Z = A + i B, A and B the Hermitian-extended spectra of columns ta, ta + 1
+  float2 v[2][8];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int jb = j0 + JS * q;
-    float2 v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int row = jb + r * (N / 8);
-      const float2 A = herm_load<N>(in, a.ld, row, ta, oka);
-      const float2 B = herm_load<N>(in, a.ld, row, tb, okb);
-      v[r] = make_float2(A.x - B.y, A.y + B.x);
+      const float4 y = herm_load2<N>(in, a.ld, jb + r * (N / 8), ta, a.nt);
+      v[q][r] = make_float2(y.x - y.w, y.y + y.z);
     }
-    dft8<+1>(v);
+  }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) sm[(jb * 8 + r) * C + col] = v[r];
+  for (int q = 0; q < 2; ++q) {
+    const int jb = j0 + JS * q;
+    dft8<+1>(v[q]);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sm[(jb * 8 + r) * C + col] = v[q][r];
   }
   __syncthreads();
   col_pass_range<+1, LOGN, C, 1, S::NPASS - 1>(sm, a.tw, tid);
 
-  // last pass straight to global: output r of butterfly jb is trace jb + r Ns
+  // last pass straight to global: output r of butterfly jb is trace jb + r Ns;
+  // real part -> column ta, imaginary part -> column ta + 1
   constexpr int Q = S::NPASS - 1, R = S::radix(Q), NB = 16 / R, Ns = S::ns(Q);
-  float2 v[16];
+  float2 w[16];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = j0 + JS * q;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = sm[(jb + r * (N / R)) * C + col];
+    for (int r = 0; r < R; ++r) w[q * R + r] = sm[(jb + r * (N / R)) * C + col];
   }
   float* out = a.out_real + slab * a.slab_real;
   const float* ew = a.ew ? a.ew + slab * a.slab_real : nullptr;
   const float* tm = a.tmask ? a.tmask + (slab / a.slabs_per_gather) * a.nx : nullptr;
+  const bool vec = (a.nt & 1) == 0;
   float ss = 0.f;
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = j0 + JS * q;
-    if (Ns > 1) twiddle_r<R>(&v[q * R], base_twiddle<+1>(a.tw, S::tw_off(Q), jb));
-    dft_r<+1, R>(&v[q * R]);
+    if (Ns > 1) twiddle_r<R>(&w[q * R], base_twiddle<+1>(a.tw, S::tw_off(Q), jb));
+    dft_r<+1, R>(&w[q * R]);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int row = jb + r * Ns;
-      if (row < a.nx) {
-        const long long o = (long long)row * a.nt;
+      if (row < a.nx && ta < a.nt) {
+        const long long o = (long long)row * a.nt + ta;
+        float2 x = w[q * R + r];
         const float g = tm ? __ldg(tm + row) : 1.f;
-        if (oka) {
-          const float x = v[q * R + r].x * g * (ew ? __ldg(ew + o + ta) : 1.f);
-          out[o + ta] = x;
-          ss = fmaf(x, x, ss);
-        }
-        if (okb) {
-          const float x = v[q * R + r].y * g * (ew ? __ldg(ew + o + tb) : 1.f);
-          out[o + tb] = x;
-          ss = fmaf(x, x, ss);
+        if (vec && ta + 1 < a.nt) {
+          float2 e = ew ? __ldg((const float2*)(ew + o)) : make_float2(1.f, 1.f);
+          x.x *= g * e.x;
+          x.y *= g * e.y;
+          *(float2*)(out + o) = x;
+          ss = fmaf(x.x, x.x, fmaf(x.y, x.y, ss));
+        } else {
+          const float xa = x.x * g * (ew ? __ldg(ew + o) : 1.f);
+          out[o] = xa;
+          ss = fmaf(xa, xa, ss);
+          if (ta + 1 < a.nt) {
+            const float xb = x.y * g * (ew ? __ldg(ew + o + 1) : 1.f);
+            out[o + 1] = xb;
+            ss = fmaf(xb, xb, ss);
+          }
         }
       }
     }
@@ -227,8 +266,8 @@ xfft_c2r_kernel(XfftArgs a) {
 
 template <int LOGN>
 cudaError_t launch_r2c_t(const XfftArgs& a, cudaStream_t s) {
-  constexpr int N = 1 << LOGN, T = N * kCols / 16;
-  const size_t smem = (size_t)N * kCols * sizeof(float2);
+  constexpr int N = 1 << LOGN, C = cols_for<LOGN>(), T = N * C / 16;
+  const size_t smem = (size_t)N * C * sizeof(float2);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(xfft_r2c_kernel<LOGN>,
@@ -236,15 +275,15 @@ cudaError_t launch_r2c_t(const XfftArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(a.slabs, (a.nt + 2 * kCols - 1) / (2 * kCols));
+  dim3 grid(a.slabs, (a.nt + 2 * C - 1) / (2 * C));
   xfft_r2c_kernel<LOGN><<<grid, T, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int LOGN>
 cudaError_t launch_c2r_t(const XfftArgs& a, cudaStream_t s) {
-  constexpr int N = 1 << LOGN, T = N * kCols / 16;
-  const size_t smem = (size_t)N * kCols * sizeof(float2);
+  constexpr int N = 1 << LOGN, C = cols_for<LOGN>(), T = N * C / 16;
+  const size_t smem = (size_t)N * C * sizeof(float2);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(xfft_c2r_kernel<LOGN>,
@@ -252,7 +291,7 @@ cudaError_t launch_c2r_t(const XfftArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(a.slabs, (a.nt + 2 * kCols - 1) / (2 * kCols));
+  dim3 grid(a.slabs, (a.nt + 2 * C - 1) / (2 * C));
   xfft_c2r_kernel<LOGN><<<grid, T, smem, s>>>(a);
   return cudaGetLastError();
 }
