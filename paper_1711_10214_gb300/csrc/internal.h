@@ -40,6 +40,8 @@ struct RowArgs {
   const float* wt = nullptr;       // [Nt] spectral weight W(w)/(Nt Nx), 0 at unmapped bins
   const int* kmin = nullptr;       // [nv][Lh] first mapped |k| (host FP64 cone rule)
   const float2* acone = nullptr;   // [nv][Lh] cone parameter a as (hi, lo) floats
+  const unsigned* taps = nullptr;  // [nv][Lh][taps_ld] Stolt taps of |k| (see tap_word)
+  int taps_ld = 0;                 // words per (v, l) row: Nt/2 + 1 rounded up to 4
   const float2* phase = nullptr;   // [nt0][Nt] exp(-i w tau0), or null (tau0 == 0)
   int batch = 0;
 };
@@ -48,6 +50,15 @@ cudaError_t launch_xfft_r2c(const XfftArgs& a, cudaStream_t s);
 cudaError_t launch_xfft_c2r(const XfftArgs& a, cudaStream_t s);
 cudaError_t launch_stolt_fwd_rows(const RowArgs& a, cudaStream_t s);
 cudaError_t launch_stolt_adj_rows(const RowArgs& a, cudaStream_t s);
+
+// Stolt tap table: one 32-bit word per (velocity, k_x index l, |k|), |k| in
+// [0, Nt/2].  Mapped bins hold (floor(u) << 20) | round(frac(u) 2^20) with
+// u = sqrt(k^2 - a^2) evaluated in FP64 (a as in the cone rule); unmapped bins
+// (k^2 <= a^2, or |k| = Nt/2) hold kTapInvalid.
+constexpr unsigned kTapInvalid = 0xffffffffu;
+inline int taps_row_len(int Nt) { return ((Nt / 2 + 1) + 3) & ~3; }
+void build_tap_rows(const float* velocities, int nv, int Nt, int Nx, int Lh, double dt, double dx,
+                    unsigned* taps, int* kmin, float2* acone);
 
 // Twiddle tables in the layout the device passes expect (see common.cuh).
 int twiddle_table_len(int logn);
@@ -80,6 +91,7 @@ struct ashrt_plan {
   float* wt = nullptr;
   int* kmin = nullptr;
   float2* acone = nullptr;
+  unsigned* taps = nullptr;
   float2* phase = nullptr;
   // workspace
   float2* X = nullptr;       // [max_batch][P][Lh][ld]

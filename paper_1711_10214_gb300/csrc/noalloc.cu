@@ -118,6 +118,7 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
   const size_t o_wt = off;    off = align256(off + (size_t)Nt * sizeof(float));
   const size_t o_kmin = off;  off = align256(off + (size_t)nv * Lh * sizeof(int));
   const size_t o_acone = off; off = align256(off + (size_t)nv * Lh * sizeof(float2));
+  const size_t o_taps = off;  off = align256(off + (size_t)nv * Lh * taps_row_len(Nt) * sizeof(unsigned));
   const size_t o_phase = off; off = align256(off + (size_t)nt0 * Nt * sizeof(float2));
   const size_t o_X = off;     off = align256(off + (size_t)batch * P * Lh * ld * sizeof(float2));
   const size_t o_Y = off;     off = align256(off + (size_t)batch * Lh * ld * sizeof(float2));
@@ -132,7 +133,7 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
   ashrt_status st = static_scratch(&base);
   if (st != ASHRT_OK) return st;
 
-  // host tables (same definitions as ashrt_plan_create)
+  // host tables (the same builders ashrt_plan_create uses)
   std::vector<float2> twt(tw_t_len), twx(tw_x_len);
   build_twiddle_table(logNt, twt.data());
   build_twiddle_table(logNx, twx.data());
@@ -151,23 +152,8 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
   }
   std::vector<int> kmin((size_t)nv * Lh);
   std::vector<float2> acone((size_t)nv * Lh);
-  for (int i = 0; i < nv; ++i) {
-    const double v = (double)velocities[i];
-    for (int l = 0; l < Lh; ++l) {
-      const double a = ((v * (double)l) * (double)Nt) * dt / ((double)Nx * dx);
-      const double a2 = a * a;
-      long long k = Nt;
-      if (a < (double)Nt) {
-        k = (long long)std::floor(a);
-        if (k < 0) k = 0;
-        while ((double)(k * k) <= a2) ++k;
-        while (k > 0 && (double)((k - 1) * (k - 1)) > a2) --k;
-      }
-      kmin[(size_t)i * Lh + l] = (int)(k < Nt ? k : Nt);
-      const float hi = (float)a;
-      acone[(size_t)i * Lh + l] = make_float2(hi, (float)(a - (double)hi));
-    }
-  }
+  std::vector<unsigned> taps((size_t)nv * Lh * taps_row_len(Nt));
+  build_tap_rows(velocities, nv, Nt, Nx, Lh, dt, dx, taps.data(), kmin.data(), acone.data());
   std::vector<float2> phase((size_t)nt0 * Nt);
   bool shift = false;
   for (int j = 0; j < nt0; ++j) {
@@ -193,6 +179,7 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
   if (e == cudaSuccess) e = put(o_wt, wt.data(), wt.size() * sizeof(float));
   if (e == cudaSuccess) e = put(o_kmin, kmin.data(), kmin.size() * sizeof(int));
   if (e == cudaSuccess) e = put(o_acone, acone.data(), acone.size() * sizeof(float2));
+  if (e == cudaSuccess) e = put(o_taps, taps.data(), taps.size() * sizeof(unsigned));
   if (e == cudaSuccess && shift) e = put(o_phase, phase.data(), phase.size() * sizeof(float2));
   if (e != cudaSuccess) {
     set_error("ashrt_forward_static: table upload failed: %s", cudaGetErrorString(e));
@@ -235,6 +222,8 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
     ra.wt = (const float*)(base + o_wt);
     ra.kmin = (const int*)(base + o_kmin);
     ra.acone = (const float2*)(base + o_acone);
+    ra.taps = (const unsigned*)(base + o_taps);
+    ra.taps_ld = taps_row_len(Nt);
     ra.phase = shift ? (const float2*)(base + o_phase) : nullptr;
     ra.batch = batch;
     e = launch_stolt_fwd_rows(ra, s);

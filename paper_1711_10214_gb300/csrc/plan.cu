@@ -57,6 +57,47 @@ void build_twiddle_table(int logn, float2* out) {
   }
 }
 
+// Cone table and Stolt taps for every (velocity, l) row, in FP64: the same
+// expressions as the FP64 reference, a = ((v*l)*Nt)*dt/(Nx*dx), mapped iff
+// k*k > a*a, u = sqrt(k^2 - a^2).
+void build_tap_rows(const float* velocities, int nv, int Nt, int Nx, int Lh, double dt, double dx,
+                    unsigned* taps, int* kmin, float2* acone) {
+  const int H = Nt / 2, ldt = taps_row_len(Nt);
+  for (int i = 0; i < nv; ++i) {
+    const double v = (double)velocities[i];
+    for (int l = 0; l < Lh; ++l) {
+      const double a = ((v * (double)l) * (double)Nt) * dt / ((double)Nx * dx);
+      const double a2 = a * a;
+      long long km = Nt;   // a >= Nt: nothing of this row is mapped
+      if (a < (double)Nt) {
+        km = (long long)std::floor(a);
+        if (km < 0) km = 0;
+        while ((double)(km * km) <= a2) ++km;
+        while (km > 0 && (double)((km - 1) * (km - 1)) > a2) --km;
+      }
+      const size_t row = (size_t)i * Lh + l;
+      kmin[row] = (int)std::min<long long>(km, Nt);
+      const float hi = (float)a;
+      acone[row] = make_float2(hi, (float)(a - (double)hi));
+      unsigned* t = taps + row * ldt;
+      for (int k = 0; k < ldt; ++k) {
+        if (k >= H || (double)k * (double)k <= a2) {
+          t[k] = kTapInvalid;
+          continue;
+        }
+        const double u = std::sqrt((double)k * (double)k - a2);
+        long long k0 = (long long)std::floor(u);
+        long long q = std::llround((u - (double)k0) * 1048576.0);
+        if (q >= 1048576) {
+          ++k0;
+          q = 0;
+        }
+        t[k] = ((unsigned)k0 << 20) | (unsigned)q;
+      }
+    }
+  }
+}
+
 static ashrt_status cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: %s", what, cudaGetErrorString(e));
   return ASHRT_ECUDA;
@@ -69,7 +110,7 @@ static ashrt_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 static void free_plan_memory(ashrt_plan* p) {
-  void* ptrs[] = {p->tw_t, p->tw_x, p->wt, p->kmin, p->acone, p->phase, p->X, p->Y,
+  void* ptrs[] = {p->tw_t, p->tw_x, p->wt, p->kmin, p->acone, p->taps, p->phase, p->X, p->Y,
                   p->u, p->pv, p->sv, p->wminv, p->r, p->qv, p->wr, p->y,
                   p->scal, p->sel, p->flags};
   for (void* q : ptrs)
@@ -145,6 +186,8 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
   ra.wt = p->wt;
   ra.kmin = p->kmin;
   ra.acone = p->acone;
+  ra.taps = p->taps;
+  ra.taps_ld = taps_row_len(p->Nt);
   ra.phase = p->shift ? p->phase : nullptr;
   ra.batch = batch;
   prof_begin(PROF_ROWS_FWD, s);
@@ -206,6 +249,8 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
   ra.wt = p->wt;
   ra.kmin = p->kmin;
   ra.acone = p->acone;
+  ra.taps = p->taps;
+  ra.taps_ld = taps_row_len(p->Nt);
   ra.phase = p->shift ? p->phase : nullptr;
   ra.batch = batch;
   prof_begin(PROF_ROWS_ADJ, s);
@@ -356,26 +401,11 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
     if (k == Nt / 2) w = 0.0;
     wt[k] = (float)(w / ((double)Nt * (double)Nx));
   }
-  // cone: a = ((v*l)*Nt)*dt / (Nx*dx) in w-bin units; mapped iff k*k > a*a (FP64)
+  // cone table and Stolt taps (FP64, host)
   std::vector<int> kmin((size_t)nv * Lh);
   std::vector<float2> acone((size_t)nv * Lh);
-  for (int i = 0; i < nv; ++i) {
-    const double v = (double)velocities[i];
-    for (int l = 0; l < Lh; ++l) {
-      const double a = ((v * (double)l) * (double)Nt) * dt / ((double)Nx * dx);
-      const double a2 = a * a;
-      long long k = Nt;   // a >= Nt: nothing of this row is mapped
-      if (a < (double)Nt) {
-        k = (long long)std::floor(a);
-        if (k < 0) k = 0;
-        while ((double)(k * k) <= a2) ++k;
-        while (k > 0 && (double)((k - 1) * (k - 1)) > a2) --k;
-      }
-      kmin[(size_t)i * Lh + l] = (int)std::min<long long>(k, Nt);
-      const float hi = (float)a;
-      acone[(size_t)i * Lh + l] = make_float2(hi, (float)(a - (double)hi));
-    }
-  }
+  std::vector<unsigned> taps((size_t)nv * Lh * taps_row_len(Nt));
+  build_tap_rows(velocities, nv, Nt, Nx, Lh, dt, dx, taps.data(), kmin.data(), acone.data());
   // asymptote shift T: exp(-i w tau0), w = 2 pi kk / (Nt dt)
   std::vector<float2> phase((size_t)nt0 * Nt);
   bool shift = false;
@@ -403,6 +433,7 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
   chk(upload(&p->wt, wt, &total));
   chk(upload(&p->kmin, kmin, &total));
   chk(upload(&p->acone, acone, &total));
+  chk(upload(&p->taps, taps, &total));
   chk(upload(&p->phase, phase, &total));
   const size_t B = (size_t)p->max_batch;
   const size_t xpan = (size_t)Lh * p->ld;

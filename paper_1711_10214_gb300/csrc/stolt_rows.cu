@@ -22,10 +22,11 @@
 // and the next panel's rows are staged with cp.async while the current one
 // is transformed.
 //
-// Cone membership (k^2 > a^2, strict; never the w-Nyquist bin) comes from
-// the host's FP64 table kmin[v][l], so the GPU and the FP64 oracle agree on
-// every bin; the fractional index u = sqrt((|k| - a)(|k| + a)) is evaluated
-// in FP32 with a carried as a (hi, lo) pair of floats.
+// The Stolt taps come from a table built on the host in FP64 (one word per
+// (v, l, |k|): floor(u) and the 20-bit fraction of u = sqrt(k^2 - a^2), or
+// "unmapped" when k^2 <= a^2), staged into shared memory with the panel, so
+// the GPU and the FP64 oracle agree on cone membership and on the taps to
+// 5e-7 in the interpolation weight.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -41,24 +42,18 @@ struct Tap {
   bool valid;
 };
 
-// Interpolation taps of output bin k (natural index in [0, N)) of one
-// (velocity, k_x) row.  For w > 0 the taps are floor(u), floor(u)+1; for
-// w < 0 the mirrored -floor(|u|), -floor(|u|)-1, which is the same linear
-// interpolation at u = -|u| (odd extension keeps real output).  A tap on the
-// w-Nyquist bin carries weight 0.
+// Interpolation taps of output bin k (natural index in [0, N)) from the tap
+// word of |k|.  For w > 0 the taps are floor(u), floor(u)+1; for w < 0 the
+// mirrored -floor(|u|), -floor(|u|)-1, which is the same linear interpolation
+// at u = -|u| (odd extension keeps real output).  A tap on the w-Nyquist bin
+// carries weight 0.
 template <int N>
-__device__ __forceinline__ Tap stolt_tap(int k, int kmin, float2 ac) {
+__device__ __forceinline__ Tap tap_decode(int k, unsigned w) {
   Tap t;
-  const int kk = k <= N / 2 ? k : k - N;
-  const int kabs = kk < 0 ? -kk : kk;
-  t.valid = (k != N / 2) && (kabs >= kmin);
-  const float fk = (float)kabs;
-  const float d1 = (fk - ac.x) - ac.y;
-  const float s1 = (fk + ac.x) + ac.y;
-  const float ua = sqrtf(fmaxf(d1 * s1, 0.f));
-  const int k0 = (int)ua;
-  const float f = ua - (float)k0;
-  if (kk > 0) {
+  t.valid = (k != N / 2) && (w != kTapInvalid);
+  const int k0 = (int)(w >> 20);
+  const float f = (float)(w & 0xfffffu) * (1.0f / 1048576.0f);
+  if (k < N / 2) {
     t.i0 = k0;
     t.i1 = k0 + 1;
   } else {
@@ -68,6 +63,11 @@ __device__ __forceinline__ Tap stolt_tap(int k, int kmin, float2 ac) {
   t.w0 = 1.f - f;
   t.w1 = (t.i1 == N / 2) ? 0.f : f;
   return t;
+}
+
+template <int N>
+__device__ __forceinline__ int kabs_of(int k) {
+  return k <= N / 2 ? k : N - k;
 }
 
 // 16-byte asynchronous global -> shared copies (Ampere-style cp.async; no
@@ -87,7 +87,12 @@ __device__ __forceinline__ void stage_rows(float2* stage, const float2* rowA, co
   for (int c = tid; c < chunks; c += T) cp_async16(stage + 2 * c, rowA + 2 * c);
   if (rowB)
     for (int c = tid; c < chunks; c += T) cp_async16(stage + ld + 2 * c, rowB + 2 * c);
-  cp_async_commit();
+}
+
+// Stage one tap row (taps_ld words, a multiple of 4; 16-byte aligned).
+__device__ __forceinline__ void stage_taps(unsigned* dst, const unsigned* src, int taps_ld, int tid,
+                                           int T) {
+  for (int c = tid; c < (taps_ld >> 2); c += T) cp_async16(dst + 4 * c, src + 4 * c);
 }
 
 template <int N>
@@ -114,6 +119,8 @@ stolt_fwd_rows(RowArgs a) {
   extern __shared__ float4 smem4[];
   float4* buf = smem4;                         // N interleaved (A, B) complex values
   float2* stage = (float2*)(smem4 + N);        // next panel: row A [ld], row B [ld]
+  unsigned* stap0 = (unsigned*)(stage + 2 * a.ld);   // tap rows, double-buffered by panel
+  unsigned* stap1 = stap0 + a.taps_ld;
   const int tid = threadIdx.x, l = blockIdx.x, b0 = 2 * blockIdx.y;
   const bool hasB = b0 + 1 < a.batch;
   const float2* xA = a.X + (long long)b0 * a.x_batch + (long long)l * a.ld;
@@ -126,10 +133,15 @@ stolt_fwd_rows(RowArgs a) {
     acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
     ph[s] = make_float2(1.f, 0.f);
   }
+  const unsigned* trow = a.taps + (long long)l * a.taps_ld;   // velocity iv: + iv * Lh * taps_ld
+  const long long tstep = (long long)a.Lh * a.taps_ld;
   stage_rows(stage, xA, xB, a.ld, tid, T);
+  stage_taps(stap0, trow, a.taps_ld, tid, T);
+  cp_async_commit();
 
   int iv = 0, jt = 0;
   for (int p = 0; p < a.P; ++p) {
+    unsigned* stap = (p & 1) ? stap1 : stap0;
     cp_async_wait_all();
     __syncthreads();
     float4 v[8];
@@ -143,7 +155,10 @@ stolt_fwd_rows(RowArgs a) {
     __syncthreads();
     if (p + 1 < a.P) {
       const long long o = (long long)(p + 1) * a.x_panel;
+      const int ivn = iv + 1 == a.nv ? 0 : iv + 1;
       stage_rows(stage, xA + o, hasB ? xB + o : nullptr, a.ld, tid, T);
+      stage_taps((p & 1) ? stap0 : stap1, trow + ivn * tstep, a.taps_ld, tid, T);
+      cp_async_commit();
     }
     if (SHIFT && iv == 0) {
 #pragma unroll
@@ -152,11 +167,10 @@ stolt_fwd_rows(RowArgs a) {
     row_first_pass<-1, N>(buf, v, tid);
     row_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw, tid);
 
-    const int km = __ldg(a.kmin + iv * a.Lh + l);
-    const float2 ac = __ldg(a.acone + iv * a.Lh + l);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      const Tap t = stolt_tap<N>(tid + T * s, km, ac);
+      const int k = tid + T * s;
+      const Tap t = tap_decode<N>(k, stap[kabs_of<N>(k)]);
       if (t.valid) {
         float4 vk = cscale(buf[swz4(t.i0)], t.w0);
         vk = cfma(t.w1, buf[swz4(t.i1)], vk);
@@ -179,122 +193,98 @@ stolt_fwd_rows(RowArgs a) {
   row_last_pass_global<+1, LOGN>(buf, a.tw, tid, yA, hasB ? yA + a.y_batch : nullptr, a.nt);
 }
 
-// Adds (atomic) or stores (exclusive) one merged contribution of the
-// adjoint scatter.  The w-Nyquist target only ever receives zero weight.
-__device__ __forceinline__ void scatter_flush(float4* buf, int target, float4 v, bool atomic,
-                                              bool hasB, int N) {
-  const int t = target & (N - 1);
-  if (t == (N >> 1)) return;
-  float4* q = &buf[swz4(t)];
-  if (!atomic) {
-    *q = v;
-    return;
-  }
-  float* f = (float*)q;
-  atomicAdd(f + 0, v.x);
-  atomicAdd(f + 1, v.y);
-  if (hasB) {
-    atomicAdd(f + 2, v.z);
-    atomicAdd(f + 3, v.w);
-  }
-}
-
-// Adjoint rows: the exact transpose.  The data rows of the gather pair are
-// transformed once.  For every panel each mapped source bin k sends its
-// weighted value to its two interpolation taps.  The fractional index u(k)
-// (FP32, monotone in |k|) makes the taps of ascending sources ascend, so each
-// thread owns 8 contiguous source bins, merges the contributions of its
-// sources to equal targets in registers, and writes its targets in order:
-// targets only it touches with plain stores, the first two and last two
-// (which a neighbouring thread may share) with shared-memory atomics.
+// Adjoint rows: the exact transpose, in gather form.  The data rows of the
+// gather pair are transformed once and kept in shared memory (weighted by W).
+// For every panel, thread t computes the output bins j = t + T s of the
+// w_tau spectrum.  With J = |j|, bin j receives (1 - f) D(k) from every
+// source k on its side of the spectrum with floor(u(|k|)) = J and f D(k) from
+// every source with floor(u(|k|)) = J - 1 (bin 0 takes the primary taps of
+// both sides).  floor(u) is non-decreasing in |k|, so those sources are one
+// run of |k| starting at the first |k| with floor(u) >= J - 1: located from
+// the inverse |k| = sqrt(J^2 + a^2) and corrected on the staged tap row.
+// Every bin is written once, by its owner: no atomics, no clearing pass, and
+// the strided ownership spreads the bins outside the cone over all warps.
 template <int LOGN, bool SHIFT, int MINB>
 __global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
 stolt_adj_rows(RowArgs a) {
-  constexpr int N = 1 << LOGN, T = N / 8;
+  constexpr int N = 1 << LOGN, T = N / 8, H = N / 2;
   using S = Sched<LOGN>;
   extern __shared__ float4 smem4[];
-  float4* buf = smem4;
+  float4* buf = smem4;                          // per-panel w_tau spectrum, then its inverse FFT
+  float4* dsp = smem4 + N;                      // data spectrum x W (both gathers)
+  unsigned* stap = (unsigned*)(smem4 + 2 * N);  // tap row of the current panel
   const int tid = threadIdx.x, l = blockIdx.x, b0 = 2 * blockIdx.y;
   const bool hasB = b0 + 1 < a.batch;
   const float2* yA = a.Y + (long long)b0 * a.y_batch + (long long)l * a.ld;
+  const unsigned* trow = a.taps + (long long)l * a.taps_ld;
+  const long long tstep = (long long)a.Lh * a.taps_ld;
+  stage_taps(stap, trow, a.taps_ld, tid, T);
+  cp_async_commit();
 
   float4 v[8];
   load_pair<N>(v, yA, hasB ? yA + a.y_batch : nullptr, a.nt, tid);
   row_first_pass<-1, N>(buf, v, tid);
   row_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw, tid);
-  // own sources: the contiguous bins k = 8 tid + s
-  float4 ds[8];
-  float2 ph[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
-    const int k = 8 * tid + s;
-    ds[s] = cscale(buf[swz4(k)], __ldg(a.wt + k));
-    ph[s] = make_float2(1.f, 0.f);
+    const int k = tid + T * s;
+    dsp[swz4(k)] = cscale(buf[swz4(k)], __ldg(a.wt + k));
   }
-  __syncthreads();
 
   float2* xA = a.Xw + (long long)b0 * a.x_batch + (long long)l * a.ld;
   float2* xB = hasB ? xA + a.x_batch : nullptr;
   int iv = 0, jt = 0;
   for (int p = 0; p < a.P; ++p) {
-    if (SHIFT && iv == 0) {
-#pragma unroll
-      for (int s = 0; s < 8; ++s) ph[s] = cconj(__ldg(a.phase + (long long)jt * N + 8 * tid + s));
-    }
-#pragma unroll
-    for (int s = 0; s < 8; ++s) buf[swz4(tid + T * s)] = make_float4(0.f, 0.f, 0.f, 0.f);
+    cp_async_wait_all();
     __syncthreads();
     const int km = __ldg(a.kmin + iv * a.Lh + l);
     const float2 ac = __ldg(a.acone + iv * a.Lh + l);
-    // running window over the two consecutive targets (cur, cur + 1)
-    int cur = -1, nflush = 0;
-    float4 A0 = make_float4(0.f, 0.f, 0.f, 0.f), A1 = A0;
+    const float af = ac.x + ac.y;
+    const float2* phj = SHIFT ? a.phase + (long long)jt * N : nullptr;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      const int k = 8 * tid + s;
-      const Tap t = stolt_tap<N>(k, km, ac);
-      if (!t.valid) continue;
-      // targets (base, base + 1) in unwrapped natural order with their weights
-      int base;
-      float wl, wh;
-      if (k < N / 2) {
-        base = t.i0;
-        wl = t.w0;
-        wh = t.w1;
-      } else {
-        base = t.i0 == 0 ? N - 1 : t.i0 - 1;   // = N - floor(u) - 1
-        wl = t.w1;
-        wh = t.w0;
+      const int j = tid + T * s;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j != H && km < H) {
+        const bool pos = j < H;
+        const int J = pos ? j : N - j;
+        // first |k| >= km with floor(u(|k|)) >= J - 1
+        int k = km;
+        if (J > 1) {
+          const float x = (float)(J - 1);
+          k = (int)ceilf(sqrtf(fmaf(x, x, af * af)));
+          k = min(max(k, km), H);
+          while (k > km && (int)(stap[k - 1] >> 20) >= J - 1) --k;
+          while (k < H && (int)(stap[k] >> 20) < J - 1) ++k;
+        }
+        for (; k < H; ++k) {
+          const unsigned w = stap[k];
+          const int b = (int)(w >> 20);
+          if (b > J) break;
+          const float f = (float)(w & 0xfffffu) * (1.0f / 1048576.0f);
+          const int kn = pos ? k : N - k;
+          float4 d = dsp[swz4(kn)];
+          if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
+          if (b == J) {
+            if (J == 0) {                       // bin 0: primary taps of +k and -k
+              float4 dm = dsp[swz4(N - k)];
+              if (SHIFT) dm = cmul(dm, cconj(__ldg(phj + (N - k))));
+              d = cadd(d, dm);
+            }
+            acc = cfma(1.f - f, d, acc);
+          } else {                              // b == J - 1: secondary tap
+            acc = cfma(f, d, acc);
+          }
+        }
       }
-      const float4 c = SHIFT ? cmul(ds[s], ph[s]) : ds[s];
-      if (cur < 0) {
-        cur = base;
-        A0 = cscale(c, wl);
-        A1 = cscale(c, wh);
-      } else if (base == cur) {
-        A0 = cfma(wl, c, A0);
-        A1 = cfma(wh, c, A1);
-      } else if (base == cur + 1) {
-        scatter_flush(buf, cur, A0, nflush < 2, hasB, N);
-        ++nflush;
-        cur = base;
-        A0 = cfma(wl, c, A1);
-        A1 = cscale(c, wh);
-      } else {
-        scatter_flush(buf, cur, A0, nflush < 2, hasB, N);
-        ++nflush;
-        scatter_flush(buf, cur + 1, A1, nflush < 2, hasB, N);
-        ++nflush;
-        cur = base;
-        A0 = cscale(c, wl);
-        A1 = cscale(c, wh);
-      }
-    }
-    if (cur >= 0) {
-      scatter_flush(buf, cur, A0, true, hasB, N);
-      scatter_flush(buf, cur + 1, A1, true, hasB, N);
+      buf[swz4(j)] = acc;
     }
     __syncthreads();
+    if (p + 1 < a.P) {
+      const int ivn = iv + 1 == a.nv ? 0 : iv + 1;
+      stage_taps(stap, trow + ivn * tstep, a.taps_ld, tid, T);
+      cp_async_commit();
+    }
     row_pass_range<+1, LOGN, 0, S::NPASS - 1>(buf, a.tw, tid);
     const long long o = (long long)p * a.x_panel;
     row_last_pass_global<+1, LOGN>(buf, a.tw, tid, xA + o, hasB ? xB + o : nullptr, a.nt);
@@ -320,12 +310,23 @@ cudaError_t set_smem(K kern, size_t bytes, bool& done) {
 template <int LOGN>
 __host__ __device__ constexpr int rows_minb() { return LOGN <= 11 ? 3 : 1; }
 
+// Largest dynamic shared memory a launch of the LOGN kernels may request
+// (ld <= Nt, taps row <= Nt/2 + 4 words): the attribute is set once to it.
+template <int LOGN>
+size_t smem_cap(bool fwd) {
+  constexpr int N = 1 << LOGN;
+  const size_t taps = (size_t)(N / 2 + 4) * sizeof(unsigned);
+  return fwd ? (size_t)N * sizeof(float4) + (size_t)2 * N * sizeof(float2) + 2 * taps
+             : (size_t)2 * N * sizeof(float4) + taps;
+}
+
 template <int LOGN, bool SHIFT, int MINB>
 cudaError_t launch_fwd_v(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
-  const size_t smem = (size_t)N * sizeof(float4) + (size_t)2 * N * sizeof(float2);   // ld <= N
-  cudaError_t e = set_smem(stolt_fwd_rows<LOGN, SHIFT, MINB>, smem, attr);
+  const size_t smem = (size_t)N * sizeof(float4) + (size_t)2 * a.ld * sizeof(float2) +
+                      (size_t)2 * a.taps_ld * sizeof(unsigned);
+  cudaError_t e = set_smem(stolt_fwd_rows<LOGN, SHIFT, MINB>, smem_cap<LOGN>(true), attr);
   if (e != cudaSuccess) return e;
   stolt_fwd_rows<LOGN, SHIFT, MINB><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
   return cudaGetLastError();
@@ -335,8 +336,8 @@ template <int LOGN, bool SHIFT, int MINB>
 cudaError_t launch_adj_v(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
-  const size_t smem = (size_t)N * sizeof(float4);
-  cudaError_t e = set_smem(stolt_adj_rows<LOGN, SHIFT, MINB>, smem, attr);
+  const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.taps_ld * sizeof(unsigned);
+  cudaError_t e = set_smem(stolt_adj_rows<LOGN, SHIFT, MINB>, smem_cap<LOGN>(false), attr);
   if (e != cudaSuccess) return e;
   stolt_adj_rows<LOGN, SHIFT, MINB><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
   return cudaGetLastError();
