@@ -161,6 +161,14 @@ typedef struct {
   double eps_r_fixed;     /* > 0: use this eps_r instead of the MAD rule */
   double eps_m_fixed;     /* > 0: use this eps_m instead of the max rule */
   const float* trace_mask_dev;  /* [batch][nx] sampling weights S, or NULL */
+  const float* apex_mask_dev;   /* [batch][nx] 1 = apex position present, 0 = absent: the
+                                   model panels of an absent apex are removed from the
+                                   solve (W_m^-1 = 0 there, so that model column stays 0);
+                                   NULL = all present.  Used to solve a narrower gather
+                                   inside a wider one (uneven batches). */
+  int use_graph;                /* 1: record the whole iteration sequence as a CUDA graph on
+                                   the first call and replay it while the arguments repeat
+                                   (ignored when tol > 0, which synchronises per iteration) */
 } irls_opts;
 
 /* Per-gather outcome of the robust solve. */
@@ -193,6 +201,37 @@ void irls_default_opts(irls_opts* opts);
 ashrt_status robust_irls_deblend(const ashrt_plan* plan, const float* d_dev, float* m_dev,
                                  float* drec_dev, int batch, const irls_opts* opts,
                                  irls_report* per_gather, void* stream);
+
+/*
+ * Batches of gathers with uneven trace counts (all with the same nt).  The
+ * gathers are independent (ch. 1: separation gather by gather is parallel
+ * work); packed layouts concatenate them:
+ *   data   : gather g is [nx_g][nt] at element offset nt * sum_{h<g} nx_h
+ *   model  : gather g is [nt0][nv][nx_g][nt] at offset P nt sum_{h<g} nx_h
+ * Gathers are grouped by padded width Nx (next power of two >= pad_x nx_g);
+ * each class is solved as one batch of its widest gather's width, narrower
+ * gathers padded with zero traces that are excluded from the solve (trace
+ * mask for the data side, apex mask for the model side), which reproduces the
+ * per-gather operator exactly.  opts->max_batch is the number of gathers of a
+ * class resident on the device at once (default 64); larger classes are
+ * processed in chunks.  Allocates at creation only.
+ */
+typedef struct ashrt_batch ashrt_batch;
+ashrt_status ashrt_batch_create(ashrt_batch** out, int nt, const int* nx_per_gather, int ngather,
+                                double dt, double dx, const float* velocities, int nv,
+                                const float* t0_shifts, int nt0, const ashrt_opts* opts);
+void ashrt_batch_destroy(ashrt_batch* batch);
+/* Number of Nx classes, packed data / model element counts, device bytes held. */
+ashrt_status ashrt_batch_info(const ashrt_batch* batch, int* n_classes, long long* data_elems,
+                              long long* model_elems, size_t* workspace_bytes);
+/* Forward / adjoint of every gather (packed layouts above), async on stream. */
+ashrt_status ashrt_batch_forward(ashrt_batch* batch, const float* m_dev, float* d_dev, void* stream);
+ashrt_status ashrt_batch_adjoint(ashrt_batch* batch, const float* d_dev, float* m_dev, void* stream);
+/* robust_irls_deblend of every gather (opts masks must be NULL; reports has
+ * ngather entries, may be NULL).  Requires with_solver.  Synchronises stream. */
+ashrt_status ashrt_batch_deblend(ashrt_batch* batch, const float* d_dev, float* m_dev,
+                                 float* drec_dev, const irls_opts* opts, irls_report* reports,
+                                 void* stream);
 
 /*
  * Measurement hooks (no counterpart in the paper; used to time the library's

@@ -29,7 +29,7 @@ class IrlsOpts(ctypes.Structure):
     _fields_ = [("p", c_double), ("q", c_double), ("n_outer", c_int), ("n_cg", c_int),
                 ("tol", c_double), ("b_r", c_double), ("b_m", c_double), ("mu", c_double),
                 ("warm_start_cg", c_int), ("eps_r_fixed", c_double), ("eps_m_fixed", c_double),
-                ("trace_mask_dev", c_void_p)]
+                ("trace_mask_dev", c_void_p), ("apex_mask_dev", c_void_p), ("use_graph", c_int)]
 
 
 class IrlsReport(ctypes.Structure):
@@ -82,6 +82,21 @@ def load():
                                          P(c_float), c_int, P(AshrtOpts), c_void_p, c_void_p,
                                          c_void_p, c_int, c_void_p]
     lib.ashrt_forward_static.restype = c_int
+    lib.ashrt_batch_create.argtypes = [P(c_void_p), c_int, P(c_int), c_int, c_double, c_double,
+                                       P(c_float), c_int, P(c_float), c_int, P(AshrtOpts)]
+    lib.ashrt_batch_create.restype = c_int
+    lib.ashrt_batch_destroy.argtypes = [c_void_p]
+    lib.ashrt_batch_destroy.restype = None
+    lib.ashrt_batch_info.argtypes = [c_void_p, P(c_int), P(ctypes.c_longlong),
+                                     P(ctypes.c_longlong), P(c_size_t)]
+    lib.ashrt_batch_info.restype = c_int
+    for name in ("ashrt_batch_forward", "ashrt_batch_adjoint"):
+        f = getattr(lib, name)
+        f.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+        f.restype = c_int
+    lib.ashrt_batch_deblend.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, P(IrlsOpts),
+                                        P(IrlsReport), c_void_p]
+    lib.ashrt_batch_deblend.restype = c_int
     lib.ashrt_last_error.argtypes = []
     lib.ashrt_last_error.restype = ctypes.c_char_p
     lib.ashrt_profile_enable.argtypes = [c_int]
@@ -218,7 +233,7 @@ class Plan:
         _check(load().ashrt_adjoint(self._h, _ptr(d), _ptr(m), _ptr(mask), int(batch),
                                     _stream(stream)))
 
-    def deblend(self, d, m, drec=None, batch=1, stream=None, mask=None, **kw):
+    def deblend(self, d, m, drec=None, batch=1, stream=None, mask=None, apex_mask=None, **kw):
         """robust_irls_deblend; keyword options are irls_opts fields. Returns reports."""
         lib = load()
         o = IrlsOpts()
@@ -228,6 +243,7 @@ class Plan:
                 raise TypeError("unknown irls option %r" % k)
             setattr(o, k, v)
         o.trace_mask_dev = _ptr(mask)
+        o.apex_mask_dev = _ptr(apex_mask)
         reps = (IrlsReport * int(batch))()
         _check(lib.robust_irls_deblend(self._h, _ptr(d), _ptr(m), _ptr(drec), int(batch),
                                        ctypes.byref(o), reps, _stream(stream)))
@@ -238,6 +254,73 @@ class Plan:
     def close(self):
         if self._h:
             load().ashrt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _reports(reps):
+    return [dict(outer_done=r.outer_done, applies_fwd=r.applies_fwd, applies_adj=r.applies_adj,
+                 flags=r.flags, misfit=list(r.misfit[:r.outer_done])) for r in reps]
+
+
+class Batch:
+    """Uneven batch of gathers (see ashrt_batch_create in include/ashrt.h)."""
+
+    def __init__(self, nt, nx_per_gather, dt, dx, velocities, t0s=None, pad_t=2, pad_x=2,
+                 fmax_hz=0.0, wavelet_peak_hz=0.0, max_resident=64, with_solver=False):
+        lib = load()
+        o = AshrtOpts()
+        lib.ashrt_default_opts(ctypes.byref(o))
+        o.pad_t, o.pad_x = int(pad_t), int(pad_x)
+        o.fmax_hz, o.wavelet_peak_hz = float(fmax_hz), float(wavelet_peak_hz)
+        o.max_batch, o.with_solver = int(max_resident), int(bool(with_solver))
+        self.nx = np.ascontiguousarray(np.asarray(nx_per_gather, dtype=np.int32))
+        self._v, vp = _farr(velocities)
+        if t0s is None:
+            tp, nt0 = None, 1
+        else:
+            self._t0, tp = _farr(t0s)
+            nt0 = self._t0.size
+        h = c_void_p()
+        self._h = None
+        _check(lib.ashrt_batch_create(ctypes.byref(h), int(nt), self.nx.ctypes.data_as(
+            ctypes.POINTER(c_int)), self.nx.size, float(dt), float(dx), vp, self._v.size, tp, nt0,
+            ctypes.byref(o)))
+        self._h = h.value
+        ncls, de, me, ws = c_int(), ctypes.c_longlong(), ctypes.c_longlong(), c_size_t()
+        _check(lib.ashrt_batch_info(self._h, ctypes.byref(ncls), ctypes.byref(de),
+                                    ctypes.byref(me), ctypes.byref(ws)))
+        self.n_classes, self.data_elems, self.model_elems = ncls.value, de.value, me.value
+        self.workspace_bytes = ws.value
+        self.nt, self.P = int(nt), self._v.size * nt0
+
+    def forward(self, m, d, stream=None):
+        _check(load().ashrt_batch_forward(self._h, _ptr(m), _ptr(d), _stream(stream)))
+
+    def adjoint(self, d, m, stream=None):
+        _check(load().ashrt_batch_adjoint(self._h, _ptr(d), _ptr(m), _stream(stream)))
+
+    def deblend(self, d, m, drec=None, stream=None, **kw):
+        lib = load()
+        o = IrlsOpts()
+        lib.irls_default_opts(ctypes.byref(o))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError("unknown irls option %r" % k)
+            setattr(o, k, v)
+        reps = (IrlsReport * self.nx.size)()
+        _check(lib.ashrt_batch_deblend(self._h, _ptr(d), _ptr(m), _ptr(drec), ctypes.byref(o),
+                                       reps, _stream(stream)))
+        return _reports(reps)
+
+    def close(self):
+        if self._h:
+            load().ashrt_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -72,6 +72,27 @@ enum ProfClass { PROF_XR2C = 0, PROF_ROWS_FWD = 1, PROF_ROWS_ADJ = 2, PROF_XC2R 
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s);
 void count_launches(int n);
+// While a stream capture is being recorded on this thread, launches are
+// counted into the capture (returned by prof_capture_end) and not timed.
+void prof_capture_begin();
+long long prof_capture_end();
+
+// Arguments a recorded solve graph was captured with.
+struct GraphKey {
+  const float* d = nullptr;
+  const float* m = nullptr;
+  const float* drec = nullptr;
+  int B = 0;
+  irls_opts opts{};
+  bool operator==(const GraphKey& o) const {
+    const irls_opts &a = opts, &b = o.opts;
+    return d == o.d && m == o.m && drec == o.drec && B == o.B && a.p == b.p && a.q == b.q &&
+           a.n_outer == b.n_outer && a.n_cg == b.n_cg && a.tol == b.tol && a.b_r == b.b_r &&
+           a.b_m == b.b_m && a.mu == b.mu && a.warm_start_cg == b.warm_start_cg &&
+           a.eps_r_fixed == b.eps_r_fixed && a.eps_m_fixed == b.eps_m_fixed &&
+           a.trace_mask_dev == b.trace_mask_dev && a.apex_mask_dev == b.apex_mask_dev;
+  }
+};
 
 }  // namespace ashrt
 
@@ -109,4 +130,10 @@ struct ashrt_plan {
   double* scal = nullptr;    // per-gather scalars
   unsigned int* sel = nullptr;   // per-gather selection scratch
   int* flags = nullptr;      // per-gather status flags
+  // recorded solve (robust_irls_deblend with use_graph)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  ashrt::GraphKey graph_key;
+  long long graph_kernels = 0;
+  int graph_applies_f = 0, graph_applies_a = 0;
 };

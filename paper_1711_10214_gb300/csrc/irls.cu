@@ -287,7 +287,8 @@ __global__ void k_epsm(double* scal, int B, double b_m, double eps_fixed) {
 
 // W_m^-1 = max(|m|, eps_m)^((2-q)/2) (1 when eps_m == 0); u = W_m m (warm) or 0
 __global__ void k_wm(const float* __restrict__ m, float* __restrict__ wminv, float* __restrict__ u,
-                     long long n, float q, const double* scal, int B, int warm) {
+                     long long n, float q, const double* scal, int B, int warm,
+                     const float* __restrict__ amask, int nx, int nt) {
   const int g = blockIdx.y;
   const long long off = (long long)g * n;
   const float e = (float)scal[S_EPSM * B + g];
@@ -299,8 +300,9 @@ __global__ void k_wm(const float* __restrict__ m, float* __restrict__ wminv, flo
       const float a = fmaxf(fabsf(mv), e);
       w = (q == 2.f) ? 1.f : (q == 1.f) ? sqrtf(a) : powf(a, 0.5f * (2.f - q));
     }
+    if (amask && __ldg(amask + (long long)g * nx + (i / nt) % nx) == 0.f) w = 0.f;
     wminv[off + i] = w;
-    u[off + i] = warm ? mv / w : 0.f;
+    u[off + i] = (warm && w != 0.f) ? mv / w : 0.f;
   }
 }
 
@@ -474,6 +476,8 @@ void irls_default_opts(irls_opts* o) {
   o->eps_r_fixed = 0.0;
   o->eps_m_fixed = 0.0;
   o->trace_mask_dev = nullptr;
+  o->apex_mask_dev = nullptr;
+  o->use_graph = 0;
 }
 
 ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, float* drec,
@@ -500,6 +504,7 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
   }
   cudaStream_t s = (cudaStream_t)stream;
   const float* tm = o.trace_mask_dev;
+  const float* am = o.apex_mask_dev;
   const long long nd = (long long)P->nx * P->nt;
   const long long nm = nd * P->P;
   const int nx = P->nx, nt = P->nt;
@@ -531,80 +536,124 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
     return ASHRT_ENAN;
   }
 
-  CK(cudaMemsetAsync(scal, 0, sizeof(double) * kSlots * B, s));
-  LAUNCH(k_set, (B + 127) / 128, 128, scal + S_ACTIVE * B, 1.0, B);
-  CK(cudaMemsetAsync(flags, 0, sizeof(int) * B, s));
-  std::vector<int> outer_cnt_h(B, 0);
-  CK(cudaMemsetAsync(outer_cnt, 0, sizeof(int) * B, s));
-
-  const dim3 gm(grid_for(nm, B), B), gd(grid_for(nd, B), B);
-  const float pf = (float)o.p, qf = (float)o.q, muf = (float)o.mu;
   int applies_f = 0, applies_a = 0;
+  // Everything below is asynchronous on stream s (and capturable as a graph
+  // when tol == 0: the tol rule synchronises once per outer iteration).
+  auto enqueue = [&](cudaStream_t s) -> ashrt_status {
+    CK(cudaMemsetAsync(scal, 0, sizeof(double) * kSlots * B, s));
+    LAUNCH(k_set, (B + 127) / 128, 128, scal + S_ACTIVE * B, 1.0, B);
+    CK(cudaMemsetAsync(flags, 0, sizeof(int) * B, s));
+    CK(cudaMemsetAsync(outer_cnt, 0, sizeof(int) * B, s));
 
-  for (int k = 0; k < o.n_outer; ++k) {
-    const bool warm = (k > 0) && o.warm_start_cg;
-    if (k == 0) {
-      // W_r = 1, W_m^-1 = 1, u = 0
-      CK(cudaMemsetAsync(P->u, 0, sizeof(float) * nm * B, s));
-      LAUNCH(k_wm, gm, kThreads, m, P->wminv, P->u, nm, qf, scal, B, 0);   // eps_m = 0 -> 1
-      LAUNCH(k_set, (B + 127) / 128, 128, scal + S_EPSR * B, 1.0, B);
-      LAUNCH(k_wr, gd, kThreads, d, P->wr, nd, 2.f, scal, B);              // p=2 -> 1
-    } else {
-      // r0 and the misfit were computed at the end of the previous outer iteration
-      select_median(P, r0, tm, B, 0, o.b_r, o.eps_r_fixed, s);
-      select_median(P, r0, tm, B, 1, o.b_r, o.eps_r_fixed, s);
-      LAUNCH(k_wr, gd, kThreads, r0, P->wr, nd, pf, scal, B);
-      CK(cudaMemsetAsync(scal + S_MAXM * B, 0, sizeof(double) * B, s));
-      LAUNCH(k_maxabs, gm, kThreads, m, nm, scal, B);
-      LAUNCH(k_epsm, (B + 127) / 128, 128, scal, B, o.b_m, o.eps_m_fixed);
-      LAUNCH(k_wm, gm, kThreads, m, P->wminv, P->u, nm, qf, scal, B, warm ? 1 : 0);
-    }
-    CK(cudaGetLastError());
-    // ---- CGLS on A = W_r S C L W_m^-1, b = W_r S d
-    LAUNCH(k_cg_init_r, gd, kThreads, d, P->y, P->wr, tm, P->r, nx, nt, warm ? 1 : 0);
-    CK(cudaMemsetAsync(scal + S_GAM0 * B, 0, sizeof(double) * 4 * B, s));
-    CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm, o.mu > 0 ? nullptr : scal + S_GAM0 * B, B, s));
-    ++applies_a;
-    if (o.mu > 0) LAUNCH(k_smu, gm, kThreads, P->sv, P->u, nm, muf, scal + S_GAM0 * B, B);
-    LAUNCH(k_copy_p, gm, kThreads, P->pv, P->sv, nm, scal, B, muf);
-    for (int it = 0; it < o.n_cg; ++it) {
-      // delta_it (+= ||A p||^2; the mu ||p||^2 part was added when p was formed)
-      CK(op_forward(P, P->pv, P->qv, P->wminv, P->wr, tm, scal + (S_DEL0 + (it & 1)) * B, B, s));
-      ++applies_f;
-      LAUNCH(k_upd_ur, gm, kThreads, P->u, P->pv, nm, P->r, P->qv, nd, scal, B, it);
-      const int nxt = (it + 1) & 1;
-      CK(cudaMemsetAsync(scal + (S_GAM0 + nxt) * B, 0, sizeof(double) * B, s));
-      CK(cudaMemsetAsync(scal + (S_DEL0 + nxt) * B, 0, sizeof(double) * B, s));
-      CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm,
-                    o.mu > 0 ? nullptr : scal + (S_GAM0 + nxt) * B, B, s));
-      ++applies_a;
-      if (o.mu > 0)
-        LAUNCH(k_smu, gm, kThreads, P->sv, P->u, nm, muf, scal + (S_GAM0 + nxt) * B, B);
-      LAUNCH(k_upd_p, gm, kThreads, P->pv, P->sv, nm, scal, B, it, muf);
+    const dim3 gm(grid_for(nm, B), B), gd(grid_for(nd, B), B);
+    const float pf = (float)o.p, qf = (float)o.q, muf = (float)o.mu;
+
+    for (int k = 0; k < o.n_outer; ++k) {
+      const bool warm = (k > 0) && o.warm_start_cg;
+      if (k == 0) {
+        // W_r = 1, W_m^-1 = 1, u = 0
+        CK(cudaMemsetAsync(P->u, 0, sizeof(float) * nm * B, s));
+        LAUNCH(k_wm, gm, kThreads, m, P->wminv, P->u, nm, qf, scal, B, 0, am, nx, nt);   // eps_m = 0 -> 1
+        LAUNCH(k_set, (B + 127) / 128, 128, scal + S_EPSR * B, 1.0, B);
+        LAUNCH(k_wr, gd, kThreads, d, P->wr, nd, 2.f, scal, B);              // p=2 -> 1
+      } else {
+        // r0 and the misfit were computed at the end of the previous outer iteration
+        select_median(P, r0, tm, B, 0, o.b_r, o.eps_r_fixed, s);
+        select_median(P, r0, tm, B, 1, o.b_r, o.eps_r_fixed, s);
+        LAUNCH(k_wr, gd, kThreads, r0, P->wr, nd, pf, scal, B);
+        CK(cudaMemsetAsync(scal + S_MAXM * B, 0, sizeof(double) * B, s));
+        LAUNCH(k_maxabs, gm, kThreads, m, nm, scal, B);
+        LAUNCH(k_epsm, (B + 127) / 128, 128, scal, B, o.b_m, o.eps_m_fixed);
+        LAUNCH(k_wm, gm, kThreads, m, P->wminv, P->u, nm, qf, scal, B, warm ? 1 : 0, am, nx, nt);
+      }
       CK(cudaGetLastError());
+      // ---- CGLS on A = W_r S C L W_m^-1, b = W_r S d
+      LAUNCH(k_cg_init_r, gd, kThreads, d, P->y, P->wr, tm, P->r, nx, nt, warm ? 1 : 0);
+      CK(cudaMemsetAsync(scal + S_GAM0 * B, 0, sizeof(double) * 4 * B, s));
+      CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm, o.mu > 0 ? nullptr : scal + S_GAM0 * B, B, s));
+      ++applies_a;
+      if (o.mu > 0) LAUNCH(k_smu, gm, kThreads, P->sv, P->u, nm, muf, scal + S_GAM0 * B, B);
+      LAUNCH(k_copy_p, gm, kThreads, P->pv, P->sv, nm, scal, B, muf);
+      for (int it = 0; it < o.n_cg; ++it) {
+        // delta_it (+= ||A p||^2; the mu ||p||^2 part was added when p was formed)
+        CK(op_forward(P, P->pv, P->qv, P->wminv, P->wr, tm, scal + (S_DEL0 + (it & 1)) * B, B, s));
+        ++applies_f;
+        LAUNCH(k_upd_ur, gm, kThreads, P->u, P->pv, nm, P->r, P->qv, nd, scal, B, it);
+        const int nxt = (it + 1) & 1;
+        CK(cudaMemsetAsync(scal + (S_GAM0 + nxt) * B, 0, sizeof(double) * B, s));
+        CK(cudaMemsetAsync(scal + (S_DEL0 + nxt) * B, 0, sizeof(double) * B, s));
+        CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm,
+                      o.mu > 0 ? nullptr : scal + (S_GAM0 + nxt) * B, B, s));
+        ++applies_a;
+        if (o.mu > 0)
+          LAUNCH(k_smu, gm, kThreads, P->sv, P->u, nm, muf, scal + (S_GAM0 + nxt) * B, B);
+        LAUNCH(k_upd_p, gm, kThreads, P->pv, P->sv, nm, scal, B, it, muf);
+        CK(cudaGetLastError());
+      }
+      // ---- m = W_m^-1 u, y = C L m (no mask), residual and misfit J_k
+      LAUNCH(k_model, gm, kThreads, m, P->wminv, P->u, nm, scal, B);
+      CK(op_forward(P, m, P->y, nullptr, nullptr, nullptr, nullptr, B, s));
+      ++applies_f;
+      CK(cudaMemsetAsync(scal + S_MIS * B, 0, sizeof(double) * B, s));
+      CK(cudaMemsetAsync(scal + S_NLIVE * B, 0, sizeof(double) * B, s));
+      CK(cudaMemsetAsync(scal + S_MAXR * B, 0, sizeof(double) * B, s));
+      LAUNCH(k_resid, gd, kThreads, d, P->y, tm, r0, nx, nt, pf, scal, B);
+      LAUNCH(k_outer_done, (B + 127) / 128, 128, scal, flags, outer_cnt, B, k, o.tol);
+      CK(cudaGetLastError());
+      if (o.tol > 0.0) {
+        std::vector<double> act(B);
+        CK(cudaMemcpyAsync(act.data(), scal + S_ACTIVE * B, sizeof(double) * B,
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        bool any = false;
+        for (double a : act) any = any || a != 0.0;
+        if (!any) break;
+      }
     }
-    // ---- m = W_m^-1 u, y = C L m (no mask), residual and misfit J_k
-    LAUNCH(k_model, gm, kThreads, m, P->wminv, P->u, nm, scal, B);
-    CK(op_forward(P, m, P->y, nullptr, nullptr, nullptr, nullptr, B, s));
-    ++applies_f;
-    CK(cudaMemsetAsync(scal + S_MIS * B, 0, sizeof(double) * B, s));
-    CK(cudaMemsetAsync(scal + S_NLIVE * B, 0, sizeof(double) * B, s));
-    CK(cudaMemsetAsync(scal + S_MAXR * B, 0, sizeof(double) * B, s));
-    LAUNCH(k_resid, gd, kThreads, d, P->y, tm, r0, nx, nt, pf, scal, B);
-    LAUNCH(k_outer_done, (B + 127) / 128, 128, scal, flags, outer_cnt, B, k, o.tol);
-    CK(cudaGetLastError());
-    if (o.tol > 0.0) {
-      std::vector<double> act(B);
-      CK(cudaMemcpyAsync(act.data(), scal + S_ACTIVE * B, sizeof(double) * B,
-                         cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      bool any = false;
-      for (double a : act) any = any || a != 0.0;
-      if (!any) break;
-    }
-  }
-  if (drec) CK(cudaMemcpyAsync(drec, P->y, sizeof(float) * nd * B, cudaMemcpyDeviceToDevice, s));
+    if (drec) CK(cudaMemcpyAsync(drec, P->y, sizeof(float) * nd * B, cudaMemcpyDeviceToDevice, s));
+    return ASHRT_OK;
+  };
 
+  ashrt_plan* Pm = const_cast<ashrt_plan*>(P);
+  const bool graph = o.use_graph && o.tol <= 0.0;
+  if (!graph) {
+    ashrt_status st = enqueue(s);
+    if (st != ASHRT_OK) return st;
+  } else {
+    GraphKey key;
+    key.d = d; key.m = m; key.drec = drec; key.B = B; key.opts = o;
+    if (!Pm->graph_exec || !(Pm->graph_key == key)) {
+      if (Pm->graph_exec) {
+        cudaGraphExecDestroy(Pm->graph_exec);
+        Pm->graph_exec = nullptr;
+      }
+      if (!Pm->cap_stream) CK(cudaStreamCreateWithFlags(&Pm->cap_stream, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCapture(Pm->cap_stream, cudaStreamCaptureModeThreadLocal));
+      prof_capture_begin();
+      ashrt_status st = enqueue(Pm->cap_stream);
+      const long long kernels = prof_capture_end();
+      cudaGraph_t g = nullptr;
+      cudaError_t ec = cudaStreamEndCapture(Pm->cap_stream, &g);
+      if (st != ASHRT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      CK(ec);
+      ec = cudaGraphInstantiate(&Pm->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      CK(ec);
+      Pm->graph_key = key;
+      Pm->graph_kernels = kernels;
+      Pm->graph_applies_f = applies_f;
+      Pm->graph_applies_a = applies_a;
+    }
+    CK(cudaGraphLaunch(Pm->graph_exec, s));
+    count_launches((int)Pm->graph_kernels);
+    applies_f = Pm->graph_applies_f;
+    applies_a = Pm->graph_applies_a;
+  }
+
+  std::vector<int> outer_cnt_h(B, 0);
   std::vector<double> hist((size_t)64 * B);
   std::vector<int> fl(B);
   CK(cudaMemcpyAsync(hist.data(), scal + S_HIST * B, sizeof(double) * 64 * B,

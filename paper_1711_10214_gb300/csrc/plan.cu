@@ -476,6 +476,8 @@ void ashrt_plan_destroy(ashrt_plan* p) {
   cudaGetDevice(&dev);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   free_plan_memory(p);
   cudaSetDevice(dev);
   delete p;

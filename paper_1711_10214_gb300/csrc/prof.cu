@@ -24,6 +24,8 @@ std::vector<cudaEvent_t> g_pool;
 double g_ms[kProfClasses] = {0};
 long long g_cnt[kProfClasses] = {0};
 thread_local cudaEvent_t t_start = nullptr;
+thread_local bool t_capturing = false;
+thread_local long long t_captured = 0;
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -37,19 +39,32 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
-void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void count_launches(int n) {
+  if (t_capturing) t_captured += n;
+  else g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+
+void prof_capture_begin() {
+  t_capturing = true;
+  t_captured = 0;
+}
+
+long long prof_capture_end() {
+  t_capturing = false;
+  return t_captured;
+}
 
 void prof_begin(int cls, cudaStream_t s) {
   (void)cls;
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  count_launches(1);
+  if (t_capturing || !g_prof_on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(g_mu);
   t_start = take_event();
   cudaEventRecord(t_start, s);
 }
 
 void prof_end(int cls, cudaStream_t s) {
-  if (!g_prof_on.load(std::memory_order_relaxed) || !t_start) return;
+  if (t_capturing || !g_prof_on.load(std::memory_order_relaxed) || !t_start) return;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t e = take_event();
   cudaEventRecord(e, s);
