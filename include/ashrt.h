@@ -203,6 +203,23 @@ ashrt_status robust_irls_deblend(const ashrt_plan* plan, const float* d_dev, flo
                                  irls_report* per_gather, void* stream);
 
 /*
+ * Autotuner (no counterpart in the paper): times forward+adjoint pairs of
+ * `batch` gathers on the plan's sizes for each kernel variant -- the row
+ * kernels' register cap (1, 2 or 3 resident CTAs per SM for Nt 512..2048) and
+ * the trace-axis FFT column tile (16 or 8 columns for Nx <= 512) -- and keeps
+ * the fastest in the plan.  With cache_path (a JSON-lines file, one object per
+ * device and problem shape) a cached choice is reused without timing and new
+ * choices are appended.  Allocates and frees temporary buffers; synchronises.
+ * The chosen variants are returned in rows_minb / xfft_cols (may be NULL).
+ * Every variant computes the same operator.
+ */
+ashrt_status ashrt_plan_autotune(ashrt_plan* plan, int batch, const char* cache_path,
+                                 int* rows_minb, int* xfft_cols);
+/* Sets the variants directly (rows_minb 1..3, xfft_cols 8 or 16); variants that
+ * do not apply to the plan's sizes fall back to the default kernel. */
+ashrt_status ashrt_plan_set_variant(ashrt_plan* plan, int rows_minb, int xfft_cols);
+
+/*
  * Batches of gathers with uneven trace counts (all with the same nt).  The
  * gathers are independent (ch. 1: separation gather by gather is parallel
  * work); packed layouts concatenate them:

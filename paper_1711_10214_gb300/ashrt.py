@@ -97,6 +97,11 @@ def load():
     lib.ashrt_batch_deblend.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, P(IrlsOpts),
                                         P(IrlsReport), c_void_p]
     lib.ashrt_batch_deblend.restype = c_int
+    lib.ashrt_plan_autotune.argtypes = [c_void_p, c_int, ctypes.c_char_p, ctypes.POINTER(c_int),
+                                        ctypes.POINTER(c_int)]
+    lib.ashrt_plan_autotune.restype = c_int
+    lib.ashrt_plan_set_variant.argtypes = [c_void_p, c_int, c_int]
+    lib.ashrt_plan_set_variant.restype = c_int
     lib.ashrt_last_error.argtypes = []
     lib.ashrt_last_error.restype = ctypes.c_char_p
     lib.ashrt_profile_enable.argtypes = [c_int]
@@ -232,6 +237,17 @@ class Plan:
     def adjoint(self, d, m, mask=None, batch=1, stream=None):
         _check(load().ashrt_adjoint(self._h, _ptr(d), _ptr(m), _ptr(mask), int(batch),
                                     _stream(stream)))
+
+    def autotune(self, batch=None, cache_path=None):
+        """ashrt_plan_autotune: returns (rows_minb, xfft_cols) chosen for this plan."""
+        mb, cols = c_int(), c_int()
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _check(load().ashrt_plan_autotune(self._h, int(batch or self.max_batch), path,
+                                          ctypes.byref(mb), ctypes.byref(cols)))
+        return mb.value, cols.value
+
+    def set_variant(self, rows_minb, xfft_cols):
+        _check(load().ashrt_plan_set_variant(self._h, int(rows_minb), int(xfft_cols)))
 
     def deblend(self, d, m, drec=None, batch=1, stream=None, mask=None, apex_mask=None, **kw):
         """robust_irls_deblend; keyword options are irls_opts fields. Returns reports."""

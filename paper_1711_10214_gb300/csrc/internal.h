@@ -26,6 +26,7 @@ struct XfftArgs {
   double* dot = nullptr;             // c2r: per-gather sum of squared outputs (added), or null
   const float2* tw = nullptr;        // base twiddles of length Nx
   int slabs = 0;
+  int cols = 16;                     // complex time columns per CTA: 16 or 8 (Nx <= 512)
 };
 
 // Arguments of the fused t-FFT + Stolt map + sum/spray row kernels.
@@ -44,6 +45,7 @@ struct RowArgs {
   int taps_ld = 0;                 // words per (v, l) row: Nt/2 + 1 rounded up to 4
   const float2* phase = nullptr;   // [nt0][Nt] exp(-i w tau0), or null (tau0 == 0)
   int batch = 0;
+  int minb = 3;                    // register-cap variant (resident CTAs per SM): 1, 2, 3
 };
 
 cudaError_t launch_xfft_r2c(const XfftArgs& a, cudaStream_t s);
@@ -106,6 +108,8 @@ struct ashrt_plan {
   int with_solver = 0;
   ashrt_opts opts{};
   bool shift = false;        // any nonzero tau0
+  int rows_minb = 3;         // kernel variants (autotuned; see ashrt_plan_autotune)
+  int xfft_cols = 16;
   // device tables
   float2* tw_t = nullptr;
   float2* tw_x = nullptr;

@@ -164,6 +164,7 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
   ax.slabs_per_gather = p->P;
   ax.slabs = batch * p->P;
   ax.tw = p->tw_x;
+  ax.cols = p->xfft_cols;
   prof_begin(PROF_XR2C, s);
   cudaError_t e = launch_xfft_r2c(ax, s);
   prof_end(PROF_XR2C, s);
@@ -190,6 +191,7 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
   ra.taps_ld = taps_row_len(p->Nt);
   ra.phase = p->shift ? p->phase : nullptr;
   ra.batch = batch;
+  ra.minb = p->rows_minb;
   prof_begin(PROF_ROWS_FWD, s);
   e = launch_stolt_fwd_rows(ra, s);
   prof_end(PROF_ROWS_FWD, s);
@@ -227,6 +229,7 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
   ay.slabs_per_gather = 1;
   ay.slabs = batch;
   ay.tw = p->tw_x;
+  ay.cols = p->xfft_cols;
   prof_begin(PROF_XR2C, s);
   cudaError_t e = launch_xfft_r2c(ay, s);
   prof_end(PROF_XR2C, s);
@@ -253,6 +256,7 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
   ra.taps_ld = taps_row_len(p->Nt);
   ra.phase = p->shift ? p->phase : nullptr;
   ra.batch = batch;
+  ra.minb = p->rows_minb;
   prof_begin(PROF_ROWS_ADJ, s);
   e = launch_stolt_adj_rows(ra, s);
   prof_end(PROF_ROWS_ADJ, s);

@@ -1,0 +1,188 @@
+// Fused time-axis FFT + Stolt map + velocity/asymptote sum (forward) or
+// spray (adjoint), one CTA per (gather pair, k_x) row.
+//
+// Forward, ch. 5 Eq. ch5_forward_operator / ch. 6 Eq. ch6_forward_operator,
+// for the row of wavenumber index l of gather b:
+//   for every panel p = (tau0_j, v_i):  load the x-transformed model row
+//     X_p(l, tau) (nt samples), zero-pad to Nt, FFT along tau -> M_p(w_tau),
+//     map w <- w_tau by the dispersion relation w_tau = sgn(w) sqrt(w^2 - (v k_x)^2)
+//     (ch. 5) with linear interpolation, and accumulate
+//     D(w) += exp(-i w tau0_j) V_p(w)   (T and the sums S / A)
+//   D *= W(w) (wavelet C, band limit, 1/(Nt Nx)); inverse FFT along t; keep nt.
+// Adjoint (ch. 5 Eq. ch5_adj_operator / ch. 6 Eq. ch6_adj_operator): the
+// exact transpose: FFT the data row once, weight by W, and for each panel
+// scatter every mapped bin to its two interpolation taps (transposed linear
+// weights, conjugate phase), inverse FFT, keep nt samples.
+//
+// One CTA handles one k_x row of a PAIR of gathers, the two rows interleaved
+// element by element (16-byte shared accesses; twiddles and Stolt taps
+// computed once for both).  The panel spectrum, the map and the accumulation
+// never leave the SM: the accumulator D lives in registers (each thread owns
+// bins k = tid + T s), the spectrum of the current panel in one shared row,
+// and the next panel's rows are staged with cp.async while the current one
+// is transformed.
+//
+// The Stolt taps come from a table built on the host in FP64 (one word per
+// (v, l, |k|): floor(u) and the 20-bit fraction of u = sqrt(k^2 - a^2), or
+// "unmapped" when k^2 <= a^2), staged into shared memory with the panel, so
+// the GPU and the FP64 oracle agree on cone membership and on the taps to
+// 5e-7 in the interpolation weight.
+#include <cuda_runtime.h>
+
+#include "stolt_common.cuh"
+
+namespace ashrt {
+
+namespace {
+
+// Adjoint rows: the exact transpose, in gather form.  The data rows of the
+// gather pair are transformed once and kept in shared memory (weighted by W).
+// For every panel, thread t computes the output bins j = t + T s of the
+// w_tau spectrum.  With J = |j|, bin j receives (1 - f) D(k) from every
+// source k on its side of the spectrum with floor(u(|k|)) = J and f D(k) from
+// every source with floor(u(|k|)) = J - 1 (bin 0 takes the primary taps of
+// both sides).  floor(u) is non-decreasing in |k|, so those sources are one
+// run of |k| starting at the first |k| with floor(u) >= J - 1: located from
+// the inverse |k| = sqrt(J^2 + a^2) and corrected on the staged tap row.
+// Every bin is written once, by its owner: no atomics, no clearing pass, and
+// the strided ownership spreads the bins outside the cone over all warps.
+template <int LOGN, bool SHIFT, int MINB>
+__global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
+stolt_adj_rows(RowArgs a) {
+  constexpr int N = 1 << LOGN, T = N / 8, H = N / 2;
+  using S = Sched<LOGN>;
+  extern __shared__ float4 smem4[];
+  float4* buf = smem4;                          // per-panel w_tau spectrum, then its inverse FFT
+  float4* dsp = smem4 + N;                      // data spectrum x W (both gathers)
+  unsigned* stap = (unsigned*)(smem4 + 2 * N);  // tap row of the current panel
+  const int tid = threadIdx.x, l = blockIdx.x, b0 = 2 * blockIdx.y;
+  const bool hasB = b0 + 1 < a.batch;
+  const float2* yA = a.Y + (long long)b0 * a.y_batch + (long long)l * a.ld;
+  const unsigned* trow = a.taps + (long long)l * a.taps_ld;
+  const long long tstep = (long long)a.Lh * a.taps_ld;
+  stage_taps(stap, trow, a.taps_ld, tid, T);
+  cp_async_commit();
+
+  float4 v[8];
+  load_pair<N>(v, yA, hasB ? yA + a.y_batch : nullptr, a.nt, tid);
+  row_first_pass<-1, N>(buf, v, tid);
+  row_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw, tid);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int k = tid + T * s;
+    dsp[swz4(k)] = cscale(buf[swz4(k)], __ldg(a.wt + k));
+  }
+
+  float2* xA = a.Xw + (long long)b0 * a.x_batch + (long long)l * a.ld;
+  float2* xB = hasB ? xA + a.x_batch : nullptr;
+  int iv = 0, jt = 0;
+  for (int p = 0; p < a.P; ++p) {
+    cp_async_wait_all();
+    __syncthreads();
+    const int km = __ldg(a.kmin + iv * a.Lh + l);
+    const float2 ac = __ldg(a.acone + iv * a.Lh + l);
+    const float af = ac.x + ac.y;
+    const float2* phj = SHIFT ? a.phase + (long long)jt * N : nullptr;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int j = tid + T * s;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j != H && km < H) {
+        const bool pos = j < H;
+        const int J = pos ? j : N - j;
+        // first |k| >= km with floor(u(|k|)) >= J - 1
+        int k = km;
+        if (J > 1) {
+          const float x = (float)(J - 1);
+          k = (int)ceilf(sqrtf(fmaf(x, x, af * af)));
+          k = min(max(k, km), H);
+          while (k > km && (int)(stap[k - 1] >> 20) >= J - 1) --k;
+          while (k < H && (int)(stap[k] >> 20) < J - 1) ++k;
+        }
+        for (; k < H; ++k) {
+          const unsigned w = stap[k];
+          const int b = (int)(w >> 20);
+          if (b > J) break;
+          const float f = (float)(w & 0xfffffu) * (1.0f / 1048576.0f);
+          const int kn = pos ? k : N - k;
+          float4 d = dsp[swz4(kn)];
+          if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
+          if (b == J) {
+            if (J == 0) {                       // bin 0: primary taps of +k and -k
+              float4 dm = dsp[swz4(N - k)];
+              if (SHIFT) dm = cmul(dm, cconj(__ldg(phj + (N - k))));
+              d = cadd(d, dm);
+            }
+            acc = cfma(1.f - f, d, acc);
+          } else {                              // b == J - 1: secondary tap
+            acc = cfma(f, d, acc);
+          }
+        }
+      }
+      buf[swz4(j)] = acc;
+    }
+    __syncthreads();
+    if (p + 1 < a.P) {
+      const int ivn = iv + 1 == a.nv ? 0 : iv + 1;
+      stage_taps(stap, trow + ivn * tstep, a.taps_ld, tid, T);
+      cp_async_commit();
+    }
+    row_pass_range<+1, LOGN, 0, S::NPASS - 1>(buf, a.tw, tid);
+    const long long o = (long long)p * a.x_panel;
+    row_last_pass_global<+1, LOGN>(buf, a.tw, tid, xA + o, hasB ? xB + o : nullptr, a.nt);
+    if (++iv == a.nv) {
+      iv = 0;
+      ++jt;
+    }
+  }
+}
+
+
+template <int LOGN, bool SHIFT, int MINB>
+cudaError_t launch_adj_v(const RowArgs& a, cudaStream_t s) {
+  constexpr int N = 1 << LOGN;
+  static bool attr = false;
+  const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.taps_ld * sizeof(unsigned);
+  cudaError_t e = set_smem(stolt_adj_rows<LOGN, SHIFT, MINB>, smem_cap<LOGN>(false), attr);
+  if (e != cudaSuccess) return e;
+  stolt_adj_rows<LOGN, SHIFT, MINB><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Register-cap variant: resident CTAs per SM the kernel is compiled for
+// (a.minb = 1: no cap; 2 or 3: caps for Nt <= 2048; Nt = 4096 CTAs have 512
+// threads and always use 1).  Chosen by the autotuner, default 3.
+template <int LOGN, bool SHIFT>
+cudaError_t launch_adj_s(const RowArgs& a, cudaStream_t s) {
+  if constexpr (LOGN >= 9 && LOGN <= 11) {
+    if (a.minb == 3) return launch_adj_v<LOGN, SHIFT, 3>(a, s);
+    if (a.minb == 2) return launch_adj_v<LOGN, SHIFT, 2>(a, s);
+    return launch_adj_v<LOGN, SHIFT, 1>(a, s);
+  } else if constexpr (LOGN < 9) {
+    return launch_adj_v<LOGN, SHIFT, 3>(a, s);
+  } else {
+    return launch_adj_v<LOGN, SHIFT, 1>(a, s);
+  }
+}
+
+template <int LOGN>
+cudaError_t launch_adj_t(const RowArgs& a, cudaStream_t s) {
+  return a.phase ? launch_adj_s<LOGN, true>(a, s) : launch_adj_s<LOGN, false>(a, s);
+}
+
+}  // namespace
+
+cudaError_t launch_stolt_adj_rows(const RowArgs& a, cudaStream_t s) {
+  switch (row_log2(a.Nt)) {
+    case 6: return launch_adj_t<6>(a, s);
+    case 7: return launch_adj_t<7>(a, s);
+    case 8: return launch_adj_t<8>(a, s);
+    case 9: return launch_adj_t<9>(a, s);
+    case 10: return launch_adj_t<10>(a, s);
+    case 11: return launch_adj_t<11>(a, s);
+    case 12: return launch_adj_t<12>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ashrt

@@ -1,0 +1,135 @@
+// Fused time-axis FFT + Stolt map + velocity/asymptote sum (forward) or
+// spray (adjoint), one CTA per (gather pair, k_x) row.
+//
+// Forward, ch. 5 Eq. ch5_forward_operator / ch. 6 Eq. ch6_forward_operator,
+// for the row of wavenumber index l of gather b:
+//   for every panel p = (tau0_j, v_i):  load the x-transformed model row
+//     X_p(l, tau) (nt samples), zero-pad to Nt, FFT along tau -> M_p(w_tau),
+//     map w <- w_tau by the dispersion relation w_tau = sgn(w) sqrt(w^2 - (v k_x)^2)
+//     (ch. 5) with linear interpolation, and accumulate
+//     D(w) += exp(-i w tau0_j) V_p(w)   (T and the sums S / A)
+//   D *= W(w) (wavelet C, band limit, 1/(Nt Nx)); inverse FFT along t; keep nt.
+// Adjoint (ch. 5 Eq. ch5_adj_operator / ch. 6 Eq. ch6_adj_operator): the
+// exact transpose: FFT the data row once, weight by W, and for each panel
+// scatter every mapped bin to its two interpolation taps (transposed linear
+// weights, conjugate phase), inverse FFT, keep nt samples.
+//
+// One CTA handles one k_x row of a PAIR of gathers, the two rows interleaved
+// element by element (16-byte shared accesses; twiddles and Stolt taps
+// computed once for both).  The panel spectrum, the map and the accumulation
+// never leave the SM: the accumulator D lives in registers (each thread owns
+// bins k = tid + T s), the spectrum of the current panel in one shared row,
+// and the next panel's rows are staged with cp.async while the current one
+// is transformed.
+//
+// The Stolt taps come from a table built on the host in FP64 (one word per
+// (v, l, |k|): floor(u) and the 20-bit fraction of u = sqrt(k^2 - a^2), or
+// "unmapped" when k^2 <= a^2), staged into shared memory with the panel, so
+// the GPU and the FP64 oracle agree on cone membership and on the taps to
+// 5e-7 in the interpolation weight.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ashrt {
+
+struct Tap {
+  int i0, i1;
+  float w0, w1;
+  bool valid;
+};
+
+// Interpolation taps of output bin k (natural index in [0, N)) from the tap
+// word of |k|.  For w > 0 the taps are floor(u), floor(u)+1; for w < 0 the
+// mirrored -floor(|u|), -floor(|u|)-1, which is the same linear interpolation
+// at u = -|u| (odd extension keeps real output).  A tap on the w-Nyquist bin
+// carries weight 0.
+template <int N>
+__device__ __forceinline__ Tap tap_decode(int k, unsigned w) {
+  Tap t;
+  t.valid = (k != N / 2) && (w != kTapInvalid);
+  const int k0 = (int)(w >> 20);
+  const float f = (float)(w & 0xfffffu) * (1.0f / 1048576.0f);
+  if (k < N / 2) {
+    t.i0 = k0;
+    t.i1 = k0 + 1;
+  } else {
+    t.i0 = (N - k0) & (N - 1);
+    t.i1 = (N - k0 - 1) & (N - 1);
+  }
+  t.w0 = 1.f - f;
+  t.w1 = (t.i1 == N / 2) ? 0.f : f;
+  return t;
+}
+
+template <int N>
+__device__ __forceinline__ int kabs_of(int k) {
+  return k <= N / 2 ? k : N - k;
+}
+
+// 16-byte asynchronous global -> shared copies (Ampere-style cp.async; no
+// waits beyond cp.async.wait_group, which the hardware completes).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// Stage the rows of gathers A and B (B may be absent) of one panel: ld
+// complex values each (ld is a multiple of 4, rows are 32-byte aligned).
+__device__ __forceinline__ void stage_rows(float2* stage, const float2* rowA, const float2* rowB,
+                                           int ld, int tid, int T) {
+  const int chunks = ld >> 1;   // 16-byte chunks of two complex values
+  for (int c = tid; c < chunks; c += T) cp_async16(stage + 2 * c, rowA + 2 * c);
+  if (rowB)
+    for (int c = tid; c < chunks; c += T) cp_async16(stage + ld + 2 * c, rowB + 2 * c);
+}
+
+// Stage one tap row (taps_ld words, a multiple of 4; 16-byte aligned).
+__device__ __forceinline__ void stage_taps(unsigned* dst, const unsigned* src, int taps_ld, int tid,
+                                           int T) {
+  for (int c = tid; c < (taps_ld >> 2); c += T) cp_async16(dst + 4 * c, src + 4 * c);
+}
+
+template <int N>
+__device__ __forceinline__ void load_pair(float4* v, const float2* __restrict__ rowA,
+                                          const float2* __restrict__ rowB, int nt, int tid) {
+  constexpr int T = N / 8;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = tid + r * T;
+    const float2 za = i < nt ? __ldg(rowA + i) : make_float2(0.f, 0.f);
+    const float2 zb = (rowB && i < nt) ? __ldg(rowB + i) : make_float2(0.f, 0.f);
+    v[r] = pack2(za, zb);
+  }
+}
+
+template <typename K>
+inline cudaError_t set_smem(K kern, size_t bytes, bool& done) {
+  if (done || bytes <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+// Largest dynamic shared memory a launch of the LOGN kernels may request
+// (ld <= Nt, taps row <= Nt/2 + 4 words): the attribute is set once to it.
+template <int LOGN>
+inline size_t smem_cap(bool fwd) {
+  constexpr int N = 1 << LOGN;
+  const size_t taps = (size_t)(N / 2 + 4) * sizeof(unsigned);
+  return fwd ? (size_t)N * sizeof(float4) + (size_t)2 * N * sizeof(float2) + 2 * taps
+             : (size_t)2 * N * sizeof(float4) + taps;
+}
+
+inline int row_log2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+}  // namespace ashrt

@@ -81,11 +81,6 @@ __device__ __forceinline__ void block_accumulate(double part, double* dst) {
   }
 }
 
-// Complex columns per CTA: 16 (32 real time samples = one 128-byte line per
-// trace) up to Nx = 512, 8 beyond so a CTA stays within 1024 threads / 64 KB.
-template <int LOGN>
-__host__ __device__ constexpr int cols_for() { return LOGN <= 9 ? 16 : 8; }
-
 // Real time samples t and t+1 of one trace, packed as z = x_t + i x_{t+1}
 // (one 8-byte load when the row is 8-byte aligned).
 __device__ __forceinline__ float2 load_pair_real(const float* __restrict__ row, int t, int nt,
@@ -94,10 +89,10 @@ __device__ __forceinline__ float2 load_pair_real(const float* __restrict__ row, 
   return make_float2(t < nt ? __ldg(row + t) : 0.f, t + 1 < nt ? __ldg(row + t + 1) : 0.f);
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) * cols_for<LOGN>() / 16)
+template <int LOGN, int C>
+__global__ void __launch_bounds__((1 << LOGN) * C / 16)
 xfft_r2c_kernel(XfftArgs a) {
-  constexpr int N = 1 << LOGN, C = cols_for<LOGN>(), T = N * C / 16, JS = T / C;
+  constexpr int N = 1 << LOGN, T = N * C / 16, JS = T / C;
   using S = Sched<LOGN>;
   extern __shared__ float2 sm[];   // [N][C]
   const int tid = threadIdx.x, col = tid % C, j0 = tid / C;
@@ -182,10 +177,10 @@ __device__ __forceinline__ float4 herm_load2(const float2* __restrict__ base, in
   return make_float4(ok ? y.x : 0.f, ok ? y.y * sy : 0.f, okb ? y.z : 0.f, okb ? y.w * sy : 0.f);
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) * cols_for<LOGN>() / 16)
+template <int LOGN, int C>
+__global__ void __launch_bounds__((1 << LOGN) * C / 16)
 xfft_c2r_kernel(XfftArgs a) {
-  constexpr int N = 1 << LOGN, C = cols_for<LOGN>(), T = N * C / 16, JS = T / C;
+  constexpr int N = 1 << LOGN, T = N * C / 16, JS = T / C;
   using S = Sched<LOGN>;
   extern __shared__ float2 sm[];   // [N][C]
   const int tid = threadIdx.x, col = tid % C, j0 = tid / C;
@@ -264,36 +259,54 @@ xfft_c2r_kernel(XfftArgs a) {
   if (a.dot) block_accumulate((double)ss, a.dot + slab / a.slabs_per_gather);
 }
 
-template <int LOGN>
-cudaError_t launch_r2c_t(const XfftArgs& a, cudaStream_t s) {
-  constexpr int N = 1 << LOGN, C = cols_for<LOGN>(), T = N * C / 16;
+template <int LOGN, int C>
+cudaError_t launch_r2c_v(const XfftArgs& a, cudaStream_t s) {
+  constexpr int N = 1 << LOGN, T = N * C / 16;
   const size_t smem = (size_t)N * C * sizeof(float2);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(xfft_r2c_kernel<LOGN>,
+    cudaError_t e = cudaFuncSetAttribute(xfft_r2c_kernel<LOGN, C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid(a.slabs, (a.nt + 2 * C - 1) / (2 * C));
-  xfft_r2c_kernel<LOGN><<<grid, T, smem, s>>>(a);
+  xfft_r2c_kernel<LOGN, C><<<grid, T, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int LOGN, int C>
+cudaError_t launch_c2r_v(const XfftArgs& a, cudaStream_t s) {
+  constexpr int N = 1 << LOGN, T = N * C / 16;
+  const size_t smem = (size_t)N * C * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(xfft_c2r_kernel<LOGN, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(a.slabs, (a.nt + 2 * C - 1) / (2 * C));
+  xfft_c2r_kernel<LOGN, C><<<grid, T, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Column-tile variant: 16 complex columns per CTA (autotuner default) or 8;
+// Nx >= 1024 always uses 8 (a CTA stays within 1024 threads and 64 KB).
+template <int LOGN>
+cudaError_t launch_r2c_t(const XfftArgs& a, cudaStream_t s) {
+  if constexpr (LOGN <= 9) {
+    if (a.cols == 16) return launch_r2c_v<LOGN, 16>(a, s);
+  }
+  return launch_r2c_v<LOGN, 8>(a, s);
 }
 
 template <int LOGN>
 cudaError_t launch_c2r_t(const XfftArgs& a, cudaStream_t s) {
-  constexpr int N = 1 << LOGN, C = cols_for<LOGN>(), T = N * C / 16;
-  const size_t smem = (size_t)N * C * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(xfft_c2r_kernel<LOGN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  if constexpr (LOGN <= 9) {
+    if (a.cols == 16) return launch_c2r_v<LOGN, 16>(a, s);
   }
-  dim3 grid(a.slabs, (a.nt + 2 * C - 1) / (2 * C));
-  xfft_c2r_kernel<LOGN><<<grid, T, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_c2r_v<LOGN, 8>(a, s);
 }
 
 }  // namespace

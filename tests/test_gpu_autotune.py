@@ -1,0 +1,56 @@
+"""Autotuner: every kernel variant computes the same operator (parity with
+the FP64 oracle for each), the tuner picks one of them and caches it."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import stolt
+
+pytestmark = pytest.mark.gpu
+DT, DX = 0.004, 12.5
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_every_variant_matches_oracle(lib):
+    import torch
+    from paper_1711_10214_gb300 import ashrt
+    nt, nx, v, B = 300, 100, [1500.0, 2600.0], 3      # Nt 1024, Nx 256: all variants apply
+    plan = ashrt.Plan(nt, nx, DT, DX, v, max_batch=B, wavelet_peak_hz=20.0)
+    g = stolt.Geometry(nt, nx, DT, DX, v, wavelet_peak_hz=20.0)
+    rng = np.random.default_rng(31)
+    m = rng.standard_normal((B,) + g.model_shape).astype(np.float32)
+    d = rng.standard_normal((B,) + g.data_shape).astype(np.float32)
+    ref_d = stolt.forward_batch(g, m)
+    ref_m = stolt.adjoint_batch(g, d)
+    dev = torch.device("cuda:0")
+    md, dd = torch.from_numpy(m).to(dev), torch.from_numpy(d).to(dev)
+    for minb in (1, 2, 3):
+        for cols in (8, 16):
+            plan.set_variant(minb, cols)
+            od, om = torch.empty_like(dd), torch.empty_like(md)
+            plan.forward(md, od, batch=B)
+            plan.adjoint(dd, om, batch=B)
+            torch.cuda.synchronize()
+            assert _rel(od.cpu().numpy(), ref_d) <= 1e-4, (minb, cols)
+            assert _rel(om.cpu().numpy(), ref_m) <= 1e-4, (minb, cols)
+    plan.close()
+
+
+def test_autotune_choice_and_cache(lib, tmp_path):
+    from paper_1711_10214_gb300 import ashrt
+    plan = ashrt.Plan(300, 100, DT, DX, [1500.0, 2600.0], max_batch=4)
+    cache = str(tmp_path / "tune.jsonl")
+    mb, cols = plan.autotune(batch=4, cache_path=cache)
+    assert mb in (1, 2, 3) and cols in (8, 16)
+    lines = [json.loads(x) for x in open(cache)]
+    assert len(lines) == 1 and lines[0]["rows_minb"] == mb and lines[0]["xfft_cols"] == cols
+    plan2 = ashrt.Plan(300, 100, DT, DX, [1500.0, 2600.0], max_batch=4)
+    assert plan2.autotune(batch=4, cache_path=cache) == (mb, cols)
+    assert len(open(cache).readlines()) == 1           # served from the cache
+    plan.close()
+    plan2.close()
