@@ -169,6 +169,12 @@ typedef struct {
   int use_graph;                /* 1: record the whole iteration sequence as a CUDA graph on
                                    the first call and replay it while the arguments repeat
                                    (ignored when tol > 0, which synchronises per iteration) */
+  const float* m0_dev;          /* [batch][nt0][nv][nx][nt] initial model (warm start), or
+                                   NULL (cold start: m = 0, W_m = I at the first iteration).
+                                   With m0 the first iteration already reweights: W_m from
+                                   m0 and, unless wr0 is given, W_r from d - C S L m0. */
+  const float* wr0_dev;         /* [batch][nx][nt] residual weights W_r of the first
+                                   iteration (e.g. a learned prediction), or NULL */
 } irls_opts;
 
 /* Per-gather outcome of the robust solve. */

@@ -102,13 +102,19 @@ def cgls(A, AT, b, x0, niter, mu=0.0):
 
 
 def irls(fwd, adj, d, n_outer, n_cg, p=1.0, q=1.0, b_r=1.345, b_m=1.0, mu=0.0,
-         live=None, eps_r_fixed=None, eps_m_fixed=None, tol=0.0, warm_start=True):
+         live=None, eps_r_fixed=None, eps_m_fixed=None, tol=0.0, warm_start=True,
+         m0=None, wr0=None):
     """IRLS for min ||d - L m||_p^p + mu ||m||_q^q (ch. 4).
 
     fwd(m) -> data and adj(d) -> model are the (masked) operator pair; ``live``
     is a boolean array over data samples used for MAD and misfit (all True if
     None).  Returns (m, report) with report = dict(misfit=[...], outer_done,
     applies_fwd, applies_adj, d_model = fwd(m)).
+
+    Warm start (an extension for learned initial guesses; the thesis always
+    starts cold): with m0 the first outer iteration already reweights, W_m from
+    m0 and W_r from the residual of m0 (or wr0 when given); with only wr0 the
+    first iteration uses W_r = wr0 and W_m = I.
     """
     d = np.asarray(d, dtype=np.float64)
     live = np.ones(d.shape, dtype=bool) if live is None else np.asarray(live, dtype=bool)
@@ -118,13 +124,22 @@ def irls(fwd, adj, d, n_outer, n_cg, p=1.0, q=1.0, b_r=1.345, b_m=1.0, mu=0.0,
     Wr = np.ones_like(d)
     Wm_inv = np.ones_like(m)
     y = None
+    if m0 is not None:
+        m = np.array(m0, dtype=np.float64).reshape(m.shape)
+        y = fwd(m)
+        nf += 1
     for k in range(n_outer):
-        if k > 0:
-            r = np.where(live, d - y, 0.0)
-            er = eps_r_fixed if eps_r_fixed is not None else eps_residual(r[live], b_r)
-            Wr = weight(r, er, p)
+        if k > 0 or m0 is not None:
+            if k == 0 and wr0 is not None:
+                Wr = np.asarray(wr0, dtype=np.float64)
+            else:
+                r = np.where(live, d - y, 0.0)
+                er = eps_r_fixed if eps_r_fixed is not None else eps_residual(r[live], b_r)
+                Wr = weight(r, er, p)
             em = eps_m_fixed if eps_m_fixed is not None else eps_model(m, b_m)
             Wm_inv = weight_inverse(m, em, q) if em > 0.0 else np.ones_like(m)
+        elif wr0 is not None:
+            Wr = np.asarray(wr0, dtype=np.float64)
 
         def A(u, Wr=Wr, Wm_inv=Wm_inv):
             return Wr * fwd(Wm_inv * u)

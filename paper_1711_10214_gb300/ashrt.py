@@ -29,7 +29,8 @@ class IrlsOpts(ctypes.Structure):
     _fields_ = [("p", c_double), ("q", c_double), ("n_outer", c_int), ("n_cg", c_int),
                 ("tol", c_double), ("b_r", c_double), ("b_m", c_double), ("mu", c_double),
                 ("warm_start_cg", c_int), ("eps_r_fixed", c_double), ("eps_m_fixed", c_double),
-                ("trace_mask_dev", c_void_p), ("apex_mask_dev", c_void_p), ("use_graph", c_int)]
+                ("trace_mask_dev", c_void_p), ("apex_mask_dev", c_void_p), ("use_graph", c_int),
+                ("m0_dev", c_void_p), ("wr0_dev", c_void_p)]
 
 
 class IrlsReport(ctypes.Structure):
@@ -249,7 +250,8 @@ class Plan:
     def set_variant(self, rows_minb, xfft_cols):
         _check(load().ashrt_plan_set_variant(self._h, int(rows_minb), int(xfft_cols)))
 
-    def deblend(self, d, m, drec=None, batch=1, stream=None, mask=None, apex_mask=None, **kw):
+    def deblend(self, d, m, drec=None, batch=1, stream=None, mask=None, apex_mask=None, m0=None,
+                wr0=None, **kw):
         """robust_irls_deblend; keyword options are irls_opts fields. Returns reports."""
         lib = load()
         o = IrlsOpts()
@@ -260,6 +262,8 @@ class Plan:
             setattr(o, k, v)
         o.trace_mask_dev = _ptr(mask)
         o.apex_mask_dev = _ptr(apex_mask)
+        o.m0_dev = _ptr(m0)
+        o.wr0_dev = _ptr(wr0)
         reps = (IrlsReport * int(batch))()
         _check(lib.robust_irls_deblend(self._h, _ptr(d), _ptr(m), _ptr(drec), int(batch),
                                        ctypes.byref(o), reps, _stream(stream)))

@@ -92,7 +92,8 @@ struct GraphKey {
            a.n_outer == b.n_outer && a.n_cg == b.n_cg && a.tol == b.tol && a.b_r == b.b_r &&
            a.b_m == b.b_m && a.mu == b.mu && a.warm_start_cg == b.warm_start_cg &&
            a.eps_r_fixed == b.eps_r_fixed && a.eps_m_fixed == b.eps_m_fixed &&
-           a.trace_mask_dev == b.trace_mask_dev && a.apex_mask_dev == b.apex_mask_dev;
+           a.trace_mask_dev == b.trace_mask_dev && a.apex_mask_dev == b.apex_mask_dev &&
+           a.m0_dev == b.m0_dev && a.wr0_dev == b.wr0_dev;
   }
 };
 

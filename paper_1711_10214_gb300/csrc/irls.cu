@@ -478,6 +478,8 @@ void irls_default_opts(irls_opts* o) {
   o->trace_mask_dev = nullptr;
   o->apex_mask_dev = nullptr;
   o->use_graph = 0;
+  o->m0_dev = nullptr;
+  o->wr0_dev = nullptr;
 }
 
 ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, float* drec,
@@ -549,18 +551,34 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
     const float pf = (float)o.p, qf = (float)o.q, muf = (float)o.mu;
 
     for (int k = 0; k < o.n_outer; ++k) {
-      const bool warm = (k > 0) && o.warm_start_cg;
-      if (k == 0) {
-        // W_r = 1, W_m^-1 = 1, u = 0
+      const bool warm = (k > 0 || o.m0_dev) && o.warm_start_cg;
+      if (k == 0 && !o.m0_dev) {
+        // cold start: W_m^-1 = 1 (0 on absent apexes), u = 0; W_r = wr0 or 1
         CK(cudaMemsetAsync(P->u, 0, sizeof(float) * nm * B, s));
         LAUNCH(k_wm, gm, kThreads, m, P->wminv, P->u, nm, qf, scal, B, 0, am, nx, nt);   // eps_m = 0 -> 1
         LAUNCH(k_set, (B + 127) / 128, 128, scal + S_EPSR * B, 1.0, B);
-        LAUNCH(k_wr, gd, kThreads, d, P->wr, nd, 2.f, scal, B);              // p=2 -> 1
+        if (o.wr0_dev) CK(cudaMemcpyAsync(P->wr, o.wr0_dev, sizeof(float) * nd * B,
+                                          cudaMemcpyDeviceToDevice, s));
+        else LAUNCH(k_wr, gd, kThreads, d, P->wr, nd, 2.f, scal, B);      // p=2 -> 1
       } else {
-        // r0 and the misfit were computed at the end of the previous outer iteration
-        select_median(P, r0, tm, B, 0, o.b_r, o.eps_r_fixed, s);
-        select_median(P, r0, tm, B, 1, o.b_r, o.eps_r_fixed, s);
-        LAUNCH(k_wr, gd, kThreads, r0, P->wr, nd, pf, scal, B);
+        if (k == 0) {
+          // warm start: m = m0, its residual r0 = S(d - C L m0), then reweight as usual
+          CK(cudaMemcpyAsync(m, o.m0_dev, sizeof(float) * nm * B, cudaMemcpyDeviceToDevice, s));
+          CK(op_forward(P, m, P->y, nullptr, nullptr, nullptr, nullptr, B, s));
+          ++applies_f;
+          CK(cudaMemsetAsync(scal + S_MIS * B, 0, sizeof(double) * B, s));
+          CK(cudaMemsetAsync(scal + S_NLIVE * B, 0, sizeof(double) * B, s));
+          CK(cudaMemsetAsync(scal + S_MAXR * B, 0, sizeof(double) * B, s));
+          LAUNCH(k_resid, gd, kThreads, d, P->y, tm, r0, nx, nt, pf, scal, B);
+        }
+        if (k == 0 && o.wr0_dev) {
+          CK(cudaMemcpyAsync(P->wr, o.wr0_dev, sizeof(float) * nd * B, cudaMemcpyDeviceToDevice, s));
+        } else {
+          // r0 and the misfit were computed at the end of the previous outer iteration
+          select_median(P, r0, tm, B, 0, o.b_r, o.eps_r_fixed, s);
+          select_median(P, r0, tm, B, 1, o.b_r, o.eps_r_fixed, s);
+          LAUNCH(k_wr, gd, kThreads, r0, P->wr, nd, pf, scal, B);
+        }
         CK(cudaMemsetAsync(scal + S_MAXM * B, 0, sizeof(double) * B, s));
         LAUNCH(k_maxabs, gm, kThreads, m, nm, scal, B);
         LAUNCH(k_epsm, (B + 127) / 128, 128, scal, B, o.b_m, o.eps_m_fixed);

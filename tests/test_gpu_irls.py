@@ -130,3 +130,32 @@ def test_nonfinite_input_is_rejected(lib):
     with pytest.raises(ashrt.AshrtError) as e:
         plan.deblend(d, m)
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("use_m0,use_wr0", [(True, False), (False, True), (True, True)])
+def test_warm_start_parity(lib, use_m0, use_wr0):
+    """Warm start from a given model m0 and/or residual weights W_r0 (the
+    inputs a learned predictor supplies) against the oracle's warm start."""
+    import torch
+    from paper_1711_10214_gb300 import ashrt
+    nt, nx, v, B = 80, 20, [1600.0, 2500.0], 2
+    rng = np.random.default_rng(14)
+    plan = ashrt.Plan(nt, nx, DT, DX, v, max_batch=B, with_solver=True)
+    g = stolt.Geometry(nt, nx, DT, DX, v)
+    d = rng.standard_normal((B, nx, nt))
+    m0 = 0.1 * rng.standard_normal((B,) + g.model_shape)
+    wr0 = rng.uniform(0.3, 1.5, (B, nx, nt))
+    dev = torch.device("cuda:0")
+    m0g = torch.from_numpy(m0.astype(np.float32)).to(dev) if use_m0 else None
+    wr0g = torch.from_numpy(wr0.astype(np.float32)).to(dev) if use_wr0 else None
+    _, drec, reps = _run(torch, plan, d, p=1.0, q=1.0, n_outer=3, n_cg=6, m0=m0g, wr0=wr0g)
+    for b in range(B):
+        f = lambda m: stolt.forward(g, m)
+        t = lambda r: stolt.adjoint(g, r)
+        m, rep = irls.irls(f, t, d[b].astype(np.float32).astype(np.float64), n_outer=3, n_cg=6,
+                           p=1, q=1,
+                           m0=m0[b].astype(np.float32).astype(np.float64) if use_m0 else None,
+                           wr0=wr0[b].astype(np.float32).astype(np.float64) if use_wr0 else None)
+        assert _rel(drec[b], stolt.forward(g, m)) <= SEP_TOL, b
+        np.testing.assert_allclose(reps[b]["misfit"], rep["misfit"], rtol=1e-3)
+    plan.close()

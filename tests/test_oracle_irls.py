@@ -128,3 +128,20 @@ def test_robust_beats_least_squares_on_blended_gather():
         q[p] = irls.q_db(clean, rep["d_model"]) - irls.q_db(clean, blended)
     assert q[2] > 0.0
     assert q[1] > q[2] + 1.0
+
+
+def test_warm_start_at_the_solution_stays_there():
+    """Starting from the l2 solution with p = q = 2 (W = I), CGLS has nothing
+    left to do: the warm-started solve returns m0."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((30, 6))
+    b = rng.standard_normal(30)
+    f, t = _dense_ops(A)
+    x_ls = np.linalg.lstsq(A, b, rcond=None)[0]
+    x, rep = irls.irls(f, t, b, n_outer=2, n_cg=10, p=2, q=2, m0=x_ls)
+    np.testing.assert_allclose(x, x_ls, atol=1e-9)
+    # wr0 = weights: a weighted l2 solve equals the weighted least squares
+    w = rng.uniform(0.2, 2.0, 30)
+    x_w, _ = irls.irls(f, t, b, n_outer=1, n_cg=12, p=2, q=2, wr0=w)
+    ref = np.linalg.lstsq(w[:, None] * A, w * b, rcond=None)[0]
+    np.testing.assert_allclose(x_w, ref, atol=1e-9)

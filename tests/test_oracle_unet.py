@@ -1,0 +1,67 @@
+"""Pins for the FP64 U-Net reference: convolution against scipy's
+correlation, and the hand-derived backward against central finite
+differences of the loss."""
+import numpy as np
+from scipy.signal import correlate
+
+from oracle import unet
+
+TINY = (2, 3, 4, 5)
+
+
+def test_conv_is_cross_correlation():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, 3, 8, 10))
+    w = rng.standard_normal((4, 3, 3, 3))
+    b = rng.standard_normal(4)
+    y = unet.conv(x, w, b)
+    for n in range(2):
+        for o in range(4):
+            ref = sum(correlate(x[n, c], w[o, c], mode="same") for c in range(3)) + b[o]
+            np.testing.assert_allclose(y[n, o], ref, atol=1e-12)
+
+
+def test_pool_and_upsample_adjoint():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((1, 2, 8, 8))
+    y = rng.standard_normal((1, 2, 4, 4))
+    assert abs(np.sum(unet.avgpool2(x) * y) - np.sum(x * unet.avgpool2_backward(y))) < 1e-12
+    assert abs(np.sum(unet.up2(y) * x) - np.sum(y * unet.up2_backward(x))) < 1e-12
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    p = unet.init_params(rng, cin=1, cout=3, ch=TINY)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = 0.1 * rng.standard_normal(p[k].shape)
+    x = rng.standard_normal((2, 1, 16, 16))
+    t = rng.standard_normal((2, 3, 16, 16))
+    lam = [1.0, 0.5, 2.0]
+    y, cache = unet.forward(p, x, ch=TINY)
+    L, gy = unet.mse_loss(y, t, lam)
+    g = unet.backward(p, cache, gy, ch=TINY)
+    h = 1e-6
+    for k in ("enc1a.w", "enc2b.w", "botta.b", "dec3a.w", "dec1b.b", "head.w"):
+        idx = tuple(rng.integers(0, s) for s in p[k].shape)
+        old = p[k][idx]
+        p[k][idx] = old + h
+        Lp = unet.mse_loss(unet.forward(p, x, ch=TINY)[0], t, lam)[0]
+        p[k][idx] = old - h
+        Lm = unet.mse_loss(unet.forward(p, x, ch=TINY)[0], t, lam)[0]
+        p[k][idx] = old
+        num = (Lp - Lm) / (2 * h)
+        assert abs(num - g[k][idx]) <= 1e-6 * max(1.0, abs(num)), (k, num, g[k][idx])
+
+
+def test_parameter_count_is_about_one_million():
+    p = unet.init_params(np.random.default_rng(3))
+    n = sum(v.size for v in p.values())
+    assert 0.9e6 < n < 1.3e6
+
+
+def test_adam_first_step_moves_by_lr():
+    p = {"w": np.array([1.0, -2.0])}
+    g = {"w": np.array([0.3, -5.0])}
+    unet.adam_step(p, g, {}, lr=0.01)
+    np.testing.assert_allclose(p["w"], [0.99, -1.99], atol=1e-7)
