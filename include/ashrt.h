@@ -175,6 +175,9 @@ typedef struct {
                                    m0 and, unless wr0 is given, W_r from d - C S L m0. */
   const float* wr0_dev;         /* [batch][nx][nt] residual weights W_r of the first
                                    iteration (e.g. a learned prediction), or NULL */
+  float* wr_out_dev;            /* [batch][nx][nt] written at the end: the residual weights
+                                   max(|r|, eps_r)^((p-2)/2) of the final residual (what the
+                                   next outer iteration would use), or NULL */
 } irls_opts;
 
 /* Per-gather outcome of the robust solve. */
@@ -274,6 +277,58 @@ ashrt_status ashrt_batch_deblend(ashrt_batch* batch, const float* d_dev, float* 
 void ashrt_profile_enable(int on);
 int ashrt_profile_read(double* ms, long long* launches, int n);
 long long ashrt_kernel_launches(void);
+
+/*
+ * Learned warm start (no counterpart in the paper, which starts every solve
+ * from m = 0 and W = I): a 4-level convolutional U-Net that maps a
+ * pseudo-deblended gather (an H x W = nx x nt image) to out_channels maps on
+ * the same grid -- the P model panels of the initial Radon model and the log
+ * of the initial residual weights -- trained on pairs the robust solve itself
+ * produces.  Channels per level 16, 48, 96, 192; 3x3 convolutions with ReLU,
+ * 2x2 average pooling, nearest 2x upsampling, skip concatenation, 1x1 head.
+ * BF16 weights and activations, FP32 accumulation, FP32 master weights and
+ * gradients, Adam (beta 0.9, 0.999, eps 1e-8).
+ *   ashrt_unet_create: H, W multiples of 8; max_batch images per call; the
+ *     parameters are init_params (n_init values, layer by layer: weights
+ *     [cout][cin][k][k] then biases [cout]) or, if NULL, He-normal from a fixed
+ *     seed.  Allocates all device memory here (ENOMEM on failure).
+ *   ashrt_unet_param_count: number of parameters.
+ *   ashrt_unet_get: copies parameters and/or gradients of the last training
+ *     step to host arrays (either may be NULL); synchronises the device.
+ *   ashrt_unet_forward: x_dev [n][H][W] fp32 -> y_dev [n][out_channels][H][W]
+ *     fp32.  Each input is divided by its RMS; with rescale = 0 the outputs
+ *     stay in these normalised units, with rescale = 1 they are returned in
+ *     input units for an IRLS misfit power p (panels times the RMS, the last
+ *     channel as exp(y) RMS^((p-2)/2)).  Async on stream.
+ *   ashrt_unet_train_step: one Adam step (lr > 0; lr = 0 only computes the
+ *     gradients) on n pairs, targets t_dev [n][out_channels][H][W] in
+ *     normalised units, loss sum_c w_c mean (y_c - t_c)^2 with host weights
+ *     channel_weight[out_channels] (NULL = 1); *loss (may be NULL) receives
+ *     the loss before the step, which synchronises the stream.
+ * Device pointers are caller-owned; all return EINVAL on bad sizes.
+ */
+typedef struct ashrt_unet ashrt_unet;
+ashrt_status ashrt_unet_create(ashrt_unet** out, int H, int W, int out_channels, int max_batch,
+                               const float* init_params, long long n_init);
+void ashrt_unet_destroy(ashrt_unet* net);
+long long ashrt_unet_param_count(const ashrt_unet* net);
+ashrt_status ashrt_unet_get(const ashrt_unet* net, float* params, float* grads, long long n);
+ashrt_status ashrt_unet_forward(ashrt_unet* net, const float* x_dev, float* y_dev, int n,
+                                int rescale, float p, void* stream);
+ashrt_status ashrt_unet_train_step(ashrt_unet* net, const float* x_dev, const float* t_dev, int n,
+                                   const float* channel_weight, float lr, double* loss,
+                                   void* stream);
+/* Training targets in the network's units from a solve (robust_irls_deblend
+ * with wr_out_dev) of the gathers x_dev [n][H][W]: its model m_dev
+ * [n][out_channels-1][H][W] divided by the RMS of x, and log wr_dev [n][H][W]
+ * minus (p-2)/2 log RMS, into t_dev [n][out_channels][H][W].  Async. */
+ashrt_status ashrt_unet_targets(ashrt_unet* net, const float* x_dev, const float* m_dev,
+                                const float* wr_dev, float* t_dev, int n, float p, void* stream);
+/* The warm start of robust_irls_deblend for gathers x_dev [n][H][W]: the
+ * network's prediction in input units, model m0_dev [n][out_channels-1][H][W]
+ * and residual weights wr0_dev [n][H][W] (either may be NULL).  Async. */
+ashrt_status ashrt_unet_predict(ashrt_unet* net, const float* x_dev, float* m0_dev,
+                                float* wr0_dev, int n, float p, void* stream);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* ashrt_last_error(void);

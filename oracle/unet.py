@@ -21,6 +21,18 @@ import numpy as np
 CHANNELS = (16, 48, 96, 192)
 
 
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64.
+
+    bfloat16 keeps the top 16 bits of an IEEE binary32 value; rounding adds
+    0x7fff plus the lowest kept bit before truncating (finite inputs only).
+    The value is first rounded to binary32.
+    """
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def layer_specs(cin=1, cout=25, ch=CHANNELS):
     c0, c1, c2, c3 = ch
     return [("enc1a", cin, c0, 3), ("enc1b", c0, c0, 3),
@@ -89,42 +101,51 @@ def up2_backward(gy):
     return gy.reshape(n, c, h // 2, 2, w // 2, 2).sum(axis=(3, 5))
 
 
-def forward(p, x, cout=25, ch=CHANNELS):
-    """Returns (y, cache)."""
+def forward(p, x, cout=25, ch=CHANNELS, rnd=None):
+    """Returns (y, cache).
+
+    rnd (optional, e.g. bf16_round) is applied to the weights, the input and
+    every stored activation (each ReLU output and each pooled map), which
+    models a network that stores them at reduced precision; None = exact.
+    """
     cache = {}
+    q = (lambda v: v) if rnd is None else rnd
 
     def cr(name, inp):
-        z = conv(inp, p[name + ".w"], p[name + ".b"])
-        a = np.maximum(z, 0.0)
+        z = conv(inp, q(p[name + ".w"]), p[name + ".b"])
+        a = q(np.maximum(z, 0.0))
         cache[name] = (inp, a)
         return a
 
+    x = q(x)
     s1 = cr("enc1b", cr("enc1a", x))
-    s2 = cr("enc2b", cr("enc2a", avgpool2(s1)))
-    s3 = cr("enc3b", cr("enc3a", avgpool2(s2)))
-    bt = cr("bottb", cr("botta", avgpool2(s3)))
+    s2 = cr("enc2b", cr("enc2a", q(avgpool2(s1))))
+    s3 = cr("enc3b", cr("enc3a", q(avgpool2(s2))))
+    bt = cr("bottb", cr("botta", q(avgpool2(s3))))
     d3 = cr("dec3b", cr("dec3a", np.concatenate([up2(bt), s3], axis=1)))
     d2 = cr("dec2b", cr("dec2a", np.concatenate([up2(d3), s2], axis=1)))
     d1 = cr("dec1b", cr("dec1a", np.concatenate([up2(d2), s1], axis=1)))
-    y = conv(d1, p["head.w"], p["head.b"])
+    y = conv(d1, q(p["head.w"]), p["head.b"])
     cache["head"] = (d1, None)
     return y, cache
 
 
-def backward(p, cache, gy, ch=CHANNELS):
-    """Gradients of sum(gy * y) with respect to every parameter."""
+def backward(p, cache, gy, ch=CHANNELS, rnd=None):
+    """Gradients of sum(gy * y) with respect to every parameter (rnd: the
+    rounding of the weights used in the forward pass; gradients exact)."""
     c0, c1, c2, c3 = ch
     g = {}
+    q = (lambda v: v) if rnd is None else rnd
 
     def cr_back(name, ga):
         inp, a = cache[name]
         gz = ga * (a > 0.0)
-        gx, gw, gb = conv_backward(inp, p[name + ".w"], gz)
+        gx, gw, gb = conv_backward(inp, q(p[name + ".w"]), gz)
         g[name + ".w"], g[name + ".b"] = gw, gb
         return gx
 
     d1 = cache["head"][0]
-    gd1, g["head.w"], g["head.b"] = conv_backward(d1, p["head.w"], gy)
+    gd1, g["head.w"], g["head.b"] = conv_backward(d1, q(p["head.w"]), gy)
     gcat1 = cr_back("dec1a", cr_back("dec1b", gd1))
     gd2_up, gs1 = gcat1[:, :c1], gcat1[:, c1:]
     gcat2 = cr_back("dec2a", cr_back("dec2b", up2_backward(gd2_up)))

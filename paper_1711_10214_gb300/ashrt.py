@@ -30,7 +30,7 @@ class IrlsOpts(ctypes.Structure):
                 ("tol", c_double), ("b_r", c_double), ("b_m", c_double), ("mu", c_double),
                 ("warm_start_cg", c_int), ("eps_r_fixed", c_double), ("eps_m_fixed", c_double),
                 ("trace_mask_dev", c_void_p), ("apex_mask_dev", c_void_p), ("use_graph", c_int),
-                ("m0_dev", c_void_p), ("wr0_dev", c_void_p)]
+                ("m0_dev", c_void_p), ("wr0_dev", c_void_p), ("wr_out_dev", c_void_p)]
 
 
 class IrlsReport(ctypes.Structure):
@@ -103,6 +103,27 @@ def load():
     lib.ashrt_plan_autotune.restype = c_int
     lib.ashrt_plan_set_variant.argtypes = [c_void_p, c_int, c_int]
     lib.ashrt_plan_set_variant.restype = c_int
+    lib.ashrt_unet_create.argtypes = [P(c_void_p), c_int, c_int, c_int, c_int, P(c_float),
+                                      ctypes.c_longlong]
+    lib.ashrt_unet_create.restype = c_int
+    lib.ashrt_unet_destroy.argtypes = [c_void_p]
+    lib.ashrt_unet_destroy.restype = None
+    lib.ashrt_unet_param_count.argtypes = [c_void_p]
+    lib.ashrt_unet_param_count.restype = ctypes.c_longlong
+    lib.ashrt_unet_get.argtypes = [c_void_p, P(c_float), P(c_float), ctypes.c_longlong]
+    lib.ashrt_unet_get.restype = c_int
+    lib.ashrt_unet_forward.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
+                                       c_void_p]
+    lib.ashrt_unet_forward.restype = c_int
+    lib.ashrt_unet_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_int, P(c_float),
+                                          c_float, P(c_double), c_void_p]
+    lib.ashrt_unet_train_step.restype = c_int
+    lib.ashrt_unet_targets.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                                       c_float, c_void_p]
+    lib.ashrt_unet_targets.restype = c_int
+    lib.ashrt_unet_predict.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_float,
+                                       c_void_p]
+    lib.ashrt_unet_predict.restype = c_int
     lib.ashrt_last_error.argtypes = []
     lib.ashrt_last_error.restype = ctypes.c_char_p
     lib.ashrt_profile_enable.argtypes = [c_int]
@@ -251,7 +272,7 @@ class Plan:
         _check(load().ashrt_plan_set_variant(self._h, int(rows_minb), int(xfft_cols)))
 
     def deblend(self, d, m, drec=None, batch=1, stream=None, mask=None, apex_mask=None, m0=None,
-                wr0=None, **kw):
+                wr0=None, wr_out=None, **kw):
         """robust_irls_deblend; keyword options are irls_opts fields. Returns reports."""
         lib = load()
         o = IrlsOpts()
@@ -264,6 +285,7 @@ class Plan:
         o.apex_mask_dev = _ptr(apex_mask)
         o.m0_dev = _ptr(m0)
         o.wr0_dev = _ptr(wr0)
+        o.wr_out_dev = _ptr(wr_out)
         reps = (IrlsReport * int(batch))()
         _check(lib.robust_irls_deblend(self._h, _ptr(d), _ptr(m), _ptr(drec), int(batch),
                                        ctypes.byref(o), reps, _stream(stream)))
@@ -341,6 +363,81 @@ class Batch:
     def close(self):
         if self._h:
             load().ashrt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _fp(a):
+    """Pointer to a contiguous float32 numpy array (no copy)."""
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(c_float))
+
+
+class UNet:
+    """Warm-start U-Net (see ashrt_unet_create in include/ashrt.h).
+
+    ``params`` (optional) is a flat float array in the C layout: per layer the
+    weights [cout][cin][k][k] then the biases [cout].
+    """
+
+    def __init__(self, H, W, out_channels, max_batch=1, params=None):
+        lib = load()
+        h = c_void_p()
+        init, n = None, 0
+        if params is not None:
+            self._init = np.ascontiguousarray(params, dtype=np.float32)
+            init, n = _fp(self._init), self._init.size
+        _check(lib.ashrt_unet_create(ctypes.byref(h), int(H), int(W), int(out_channels),
+                                     int(max_batch), init, n))
+        self._h = h.value
+        self.H, self.W, self.out_channels, self.max_batch = H, W, out_channels, max_batch
+        self.n_params = int(lib.ashrt_unet_param_count(self._h))
+
+    def params(self):
+        out = np.empty(self.n_params, np.float32)
+        _check(load().ashrt_unet_get(self._h, _fp(out), None, self.n_params))
+        return out
+
+    def grads(self):
+        out = np.empty(self.n_params, np.float32)
+        _check(load().ashrt_unet_get(self._h, None, _fp(out), self.n_params))
+        return out
+
+    def forward(self, x, y, n=None, rescale=False, p=1.0, stream=None):
+        n = int(n if n is not None else x.shape[0])
+        _check(load().ashrt_unet_forward(self._h, _ptr(x), _ptr(y), n, int(bool(rescale)),
+                                         float(p), _stream(stream)))
+
+    def train_step(self, x, t, lr, n=None, channel_weight=None, stream=None):
+        """One Adam step (lr = 0: gradients only); returns the loss before the step."""
+        n = int(n if n is not None else x.shape[0])
+        cw = None
+        if channel_weight is not None:
+            self._cw = np.ascontiguousarray(channel_weight, dtype=np.float32)
+            cw = _fp(self._cw)
+        loss = c_double()
+        _check(load().ashrt_unet_train_step(self._h, _ptr(x), _ptr(t), n, cw, float(lr),
+                                            ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def targets(self, x, m, wr, t, n=None, p=1.0, stream=None):
+        n = int(n if n is not None else x.shape[0])
+        _check(load().ashrt_unet_targets(self._h, _ptr(x), _ptr(m), _ptr(wr), _ptr(t), n,
+                                         float(p), _stream(stream)))
+
+    def predict(self, x, m0=None, wr0=None, n=None, p=1.0, stream=None):
+        n = int(n if n is not None else x.shape[0])
+        _check(load().ashrt_unet_predict(self._h, _ptr(x), _ptr(m0), _ptr(wr0), n, float(p),
+                                         _stream(stream)))
+
+    def close(self):
+        if self._h:
+            load().ashrt_unet_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -93,7 +93,7 @@ struct GraphKey {
            a.b_m == b.b_m && a.mu == b.mu && a.warm_start_cg == b.warm_start_cg &&
            a.eps_r_fixed == b.eps_r_fixed && a.eps_m_fixed == b.eps_m_fixed &&
            a.trace_mask_dev == b.trace_mask_dev && a.apex_mask_dev == b.apex_mask_dev &&
-           a.m0_dev == b.m0_dev && a.wr0_dev == b.wr0_dev;
+           a.m0_dev == b.m0_dev && a.wr0_dev == b.wr0_dev && a.wr_out_dev == b.wr_out_dev;
   }
 };
 

@@ -480,6 +480,7 @@ void irls_default_opts(irls_opts* o) {
   o->use_graph = 0;
   o->m0_dev = nullptr;
   o->wr0_dev = nullptr;
+  o->wr_out_dev = nullptr;
 }
 
 ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, float* drec,
@@ -629,6 +630,13 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
       }
     }
     if (drec) CK(cudaMemcpyAsync(drec, P->y, sizeof(float) * nd * B, cudaMemcpyDeviceToDevice, s));
+    if (o.wr_out_dev) {
+      // the weights the next outer iteration would take from the final residual
+      select_median(P, r0, tm, B, 0, o.b_r, o.eps_r_fixed, s);
+      select_median(P, r0, tm, B, 1, o.b_r, o.eps_r_fixed, s);
+      LAUNCH(k_wr, gd, kThreads, r0, o.wr_out_dev, nd, pf, scal, B);
+      CK(cudaGetLastError());
+    }
     return ASHRT_OK;
   };
 

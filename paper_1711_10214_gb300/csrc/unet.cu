@@ -1,0 +1,881 @@
+// Learned warm start: a 4-level U-Net (the same architecture as the FP64
+// reference of the tests) with hand-written forward and backward kernels.
+// BF16 storage for weights and activations, FP32 accumulation, FP32 master
+// weights and gradients, Adam.  It maps a pseudo-deblended gather to an
+// initial Radon model (P channels) and initial IRLS residual weights
+// (log W_r, one channel) for the warm-started robust solve.
+//
+// Layouts: activations NHWC (image rows = traces x, columns = time t, so a
+// gather [nx][nt] is an nx x nt image) with a per-tensor pixel stride and
+// channel offset, so skip connections are written straight into the channel
+// slice of the concatenation buffer they feed.  Convolution weights are kept
+// in FP32 "OIHW" order (the reference's order) and converted every step to a
+// BF16 [tap][ci][co] copy (forward) and a flipped, transposed [tap][co][ci]
+// copy (gradient with respect to the input).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kPix = 128;   // pixels (along a row) per CTA
+constexpr int kCh = 16;     // input / output channel tile
+
+template <typename T>
+__device__ __forceinline__ float ld_f(const T* p, long long i);
+template <>
+__device__ __forceinline__ float ld_f<float>(const float* p, long long i) { return p[i]; }
+template <>
+__device__ __forceinline__ float ld_f<bf16>(const bf16* p, long long i) { return __bfloat162float(p[i]); }
+
+template <typename T>
+__device__ __forceinline__ void st_f(T* p, long long i, float v);
+template <>
+__device__ __forceinline__ void st_f<float>(float* p, long long i, float v) { p[i] = v; }
+template <>
+__device__ __forceinline__ void st_f<bf16>(bf16* p, long long i, float v) { p[i] = __float2bfloat16(v); }
+
+struct Tensor {        // a channel slice of an NHWC buffer
+  void* p = nullptr;
+  int ps = 0;          // channels allocated per pixel
+  int off = 0;         // first channel of the slice
+};
+
+struct ConvArgs {
+  Tensor in;           // input (bf16 activations or fp32 gradients)
+  Tensor mask;         // bf16 activation: multiply input by (mask > 0), or p == nullptr
+  const bf16* w;       // [K*K][Cin][Cout]
+  const float* bias;   // [Cout] or nullptr
+  Tensor out;
+  int N, H, W, Cin, Cout, relu;
+};
+
+// y[p, co] = bias[co] + sum_{tap, ci} x[p + tap, ci] * w[tap][ci][co], "same"
+// zero padding, optional ReLU.  CTA: 128 consecutive pixels of one image row
+// x 16 output channels; input channels in tiles of 16 staged in shared
+// memory (3 rows x 130 pixels with the halo) together with the weight tile.
+template <int K, typename TI, typename TO>
+__global__ void __launch_bounds__(kPix) k_conv(ConvArgs a) {
+  constexpr int R = K / 2, PW = kPix + 2 * R;
+  __shared__ float xs[K][kCh][PW + 1];
+  __shared__ __align__(16) float ws[K * K][kCh][kCh];
+  const int tid = threadIdx.x;
+  const int xt = (a.W + kPix - 1) / kPix;
+  const int row = blockIdx.x / xt;               // n * H + y
+  const int x0 = (blockIdx.x % xt) * kPix;
+  const int n = row / a.H, y = row % a.H;
+  const int co0 = blockIdx.y * kCh;
+  const TI* in = (const TI*)a.in.p;
+  const bf16* mk = (const bf16*)a.mask.p;
+  float acc[kCh];
+#pragma unroll
+  for (int c = 0; c < kCh; ++c) acc[c] = 0.f;
+
+  for (int ci0 = 0; ci0 < a.Cin; ci0 += kCh) {
+    for (int e = tid; e < K * PW * kCh; e += kPix) {
+      const int c = e % kCh, px = (e / kCh) % PW, r = e / (kCh * PW);
+      const int yy = y + r - R, xx = x0 + px - R, ci = ci0 + c;
+      float v = 0.f;
+      if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && ci < a.Cin) {
+        const long long pix = ((long long)n * a.H + yy) * a.W + xx;
+        v = ld_f(in, pix * a.in.ps + a.in.off + ci);
+        if (mk && __bfloat162float(mk[pix * a.mask.ps + a.mask.off + ci]) <= 0.f) v = 0.f;
+      }
+      xs[r][c][px] = v;
+    }
+    for (int e = tid; e < K * K * kCh * kCh; e += kPix) {
+      const int co = e % kCh, ci = (e / kCh) % kCh, tap = e / (kCh * kCh);
+      float v = 0.f;
+      if (ci0 + ci < a.Cin && co0 + co < a.Cout)
+        v = __bfloat162float(a.w[((long long)tap * a.Cin + ci0 + ci) * a.Cout + co0 + co]);
+      ws[tap][ci][co] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ci = 0; ci < kCh; ++ci) {
+#pragma unroll
+      for (int tap = 0; tap < K * K; ++tap) {
+        const float v = xs[tap / K][ci][tid + tap % K];
+        const float4* wp = (const float4*)&ws[tap][ci][0];
+#pragma unroll
+        for (int q = 0; q < kCh / 4; ++q) {
+          const float4 w4 = wp[q];
+          acc[4 * q + 0] = fmaf(v, w4.x, acc[4 * q + 0]);
+          acc[4 * q + 1] = fmaf(v, w4.y, acc[4 * q + 1]);
+          acc[4 * q + 2] = fmaf(v, w4.z, acc[4 * q + 2]);
+          acc[4 * q + 3] = fmaf(v, w4.w, acc[4 * q + 3]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int xx = x0 + tid;
+  if (xx >= a.W) return;
+  const long long pix = ((long long)n * a.H + y) * a.W + xx;
+  TO* out = (TO*)a.out.p;
+#pragma unroll
+  for (int c = 0; c < kCh; ++c) {
+    const int co = co0 + c;
+    if (co >= a.Cout) break;
+    float v = acc[c] + (a.bias ? a.bias[co] : 0.f);
+    if (a.relu) v = fmaxf(v, 0.f);
+    st_f(out, pix * a.out.ps + a.out.off + co, v);
+  }
+}
+
+struct WgradArgs {
+  Tensor in;          // bf16 layer input
+  Tensor g;           // fp32 gradient of the layer output
+  Tensor mask;        // bf16 layer output (ReLU mask) or p == nullptr
+  float* gw;          // [Cout][Cin][K][K] fp32 (the master weights' layout), accumulated
+  float* gb;          // [Cout] fp32, accumulated
+  int N, H, W, Cin, Cout;
+  int rows_per;       // image rows (over all N*H) one CTA reduces before its atomics
+};
+
+// gw[co][ci][tap] += sum_p x[p + tap, ci] g_eff[p, co]; gb[co] += sum_p g_eff[p, co]
+// with g_eff = g (mask > 0).  CTA: a 128-pixel column strip of rows_per image
+// rows x 16 input x 16 output channels; thread (ci, co) accumulates all K*K
+// taps over the strip, then one atomic each.
+template <int K>
+__global__ void __launch_bounds__(256) k_wgrad(WgradArgs a) {
+  constexpr int R = K / 2, PW = kPix + 2 * R;
+  __shared__ float xs[K][kCh][PW + 1];
+  __shared__ float gs[kCh][kPix + 1];
+  const int tid = threadIdx.x;
+  const int xt = (a.W + kPix - 1) / kPix;
+  const int x0 = (blockIdx.x % xt) * kPix;
+  const int row0 = (blockIdx.x / xt) * a.rows_per;
+  const int row1 = min(row0 + a.rows_per, a.N * a.H);
+  const int ci0 = blockIdx.y * kCh, co0 = blockIdx.z * kCh;
+  const bf16* in = (const bf16*)a.in.p;
+  const float* g = (const float*)a.g.p;
+  const bf16* mk = (const bf16*)a.mask.p;
+  const int ci = tid / kCh, co = tid % kCh;
+  float acc[K * K];
+#pragma unroll
+  for (int t = 0; t < K * K; ++t) acc[t] = 0.f;
+  float gsum = 0.f;
+  for (int row = row0; row < row1; ++row) {
+    const int n = row / a.H, y = row % a.H;
+    for (int e = tid; e < K * PW * kCh; e += 256) {
+      const int c = e % kCh, px = (e / kCh) % PW, r = e / (kCh * PW);
+      const int yy = y + r - R, xx = x0 + px - R, cc = ci0 + c;
+      float v = 0.f;
+      if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && cc < a.Cin)
+        v = __bfloat162float(in[(((long long)n * a.H + yy) * a.W + xx) * a.in.ps + a.in.off + cc]);
+      xs[r][c][px] = v;
+    }
+    for (int e = tid; e < kPix * kCh; e += 256) {
+      const int c = e % kCh, px = e / kCh;
+      const int xx = x0 + px, cc = co0 + c;
+      float v = 0.f;
+      if (xx < a.W && cc < a.Cout) {
+        const long long pix = ((long long)n * a.H + y) * a.W + xx;
+        v = g[pix * a.g.ps + a.g.off + cc];
+        if (mk && __bfloat162float(mk[pix * a.mask.ps + a.mask.off + cc]) <= 0.f) v = 0.f;
+      }
+      gs[c][px] = v;
+    }
+    __syncthreads();
+    for (int px = 0; px < kPix; ++px) {
+      const float gv = gs[co][px];
+      gsum += gv;
+#pragma unroll
+      for (int t = 0; t < K * K; ++t) acc[t] = fmaf(xs[t / K][ci][px + t % K], gv, acc[t]);
+    }
+    __syncthreads();
+  }
+  if (ci0 + ci < a.Cin && co0 + co < a.Cout) {
+#pragma unroll
+    for (int t = 0; t < K * K; ++t)
+      atomicAdd(&a.gw[((long long)(co0 + co) * a.Cin + ci0 + ci) * (K * K) + t], acc[t]);
+  }
+  if (ci == 0 && blockIdx.y == 0 && co0 + co < a.Cout) atomicAdd(&a.gb[co0 + co], gsum);
+}
+
+// 2x2 average pooling (forward, bf16) and its transpose (accumulated, fp32).
+__global__ void k_pool(Tensor in, Tensor out, int N, int H, int W, int C) {
+  const int Ho = H / 2, Wo = W / 2;
+  const long long total = (long long)N * Ho * Wo * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long p = i / C;
+    const int xo = (int)(p % Wo), yo = (int)((p / Wo) % Ho), n = (int)(p / ((long long)Wo * Ho));
+    float s = 0.f;
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const long long q = ((long long)n * H + 2 * yo + dy) * W + 2 * xo + dx;
+        s += __bfloat162float(((const bf16*)in.p)[q * in.ps + in.off + c]);
+      }
+    ((bf16*)out.p)[p * out.ps + out.off + c] = __float2bfloat16(0.25f * s);
+  }
+}
+
+__global__ void k_pool_bwd_acc(Tensor gout, Tensor gin, int N, int H, int W, int C) {
+  const long long total = (long long)N * H * W * C;   // H, W: full-resolution sizes
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long p = i / C;
+    const int x = (int)(p % W), y = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
+    const long long q = ((long long)n * (H / 2) + y / 2) * (W / 2) + x / 2;
+    ((float*)gin.p)[p * gin.ps + gin.off + c] += 0.25f * ((const float*)gout.p)[q * gout.ps + gout.off + c];
+  }
+}
+
+// nearest 2x upsampling (forward, bf16) and its transpose (fp32, written)
+__global__ void k_up(Tensor in, Tensor out, int N, int H, int W, int C) {   // H, W: output sizes
+  const long long total = (long long)N * H * W * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long p = i / C;
+    const int x = (int)(p % W), y = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
+    const long long q = ((long long)n * (H / 2) + y / 2) * (W / 2) + x / 2;
+    ((bf16*)out.p)[p * out.ps + out.off + c] = ((const bf16*)in.p)[q * in.ps + in.off + c];
+  }
+}
+
+__global__ void k_up_bwd(Tensor gout, Tensor gin, int N, int H, int W, int C) {   // H, W: input (low-res) sizes
+  const long long total = (long long)N * H * W * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long p = i / C;
+    const int x = (int)(p % W), y = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
+    float s = 0.f;
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const long long q = ((long long)n * (2 * H) + 2 * y + dy) * (2 * W) + 2 * x + dx;
+        s += ((const float*)gout.p)[q * gout.ps + gout.off + c];
+      }
+    ((float*)gin.p)[p * gin.ps + gin.off + c] = s;
+  }
+}
+
+// gathers [N][nx][nt] -> bf16 image [N][nx][nt][1] scaled by 1/rms[n]
+__global__ void k_pack_in(const float* d, const float* rms, bf16* x, long long per, int N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per * N;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = __float2bfloat16(d[i] / rms[i / per]);
+}
+
+__global__ void k_rms(const float* d, long long per, float* rms) {
+  const int n = blockIdx.x;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < per; i += blockDim.x) s += (double)d[n * per + i] * d[n * per + i];
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rms[n] = (float)fmax(sqrt(red[0] / (double)per), 1e-30);
+}
+
+// NHWC head output [N][P][cout] -> planar [N][cout][P] (P = pixels)
+__global__ void k_unpack_out(const float* y, float* out, long long P, int C, int N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * C * N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i % P;
+    const int c = (int)((i / P) % C);
+    const long long n = i / (P * C);
+    out[i] = y[(n * P + p) * C + c];
+  }
+}
+
+// loss = sum_c lam_c mean_p (y - t)^2 with y NHWC [N][P][C], t planar [N][C][P]
+__global__ void k_mse(const float* y, const float* t, const float* lam, float* gy, long long P,
+                      int C, int N, double* loss) {
+  const double inv = 1.0 / ((double)P * N);
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * C * N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long p = (i / C) % P, n = i / (P * C);
+    const float l = lam ? lam[c] : 1.f;
+    const float e = y[i] - t[(n * C + c) * P + p];
+    s += (double)l * e * e;
+    gy[i] = (float)(2.0 * inv) * l * e;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0] * inv);
+}
+
+// Adam on the flat FP32 master parameters
+__global__ void k_adam(float* w, const float* g, float* m, float* v, long long n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// FP32 OIHW master -> BF16 [tap][ci][co] (forward) and flipped [tap'][co][ci] (input gradient)
+__global__ void k_wconv(const float* w, bf16* wf, bf16* wt, int co_n, int ci_n, int K) {
+  const int total = co_n * ci_n * K * K;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int kx = i % K, ky = (i / K) % K, ci = (i / (K * K)) % ci_n, co = i / (K * K * ci_n);
+    const int tap = ky * K + kx, tapf = (K * K - 1) - tap;
+    const bf16 b = __float2bfloat16(w[i]);
+    wf[((long long)tap * ci_n + ci) * co_n + co] = b;
+    wt[((long long)tapf * co_n + co) * ci_n + ci] = b;
+  }
+}
+
+// Outputs back in input units: model panels (channels < C-1) scale with the
+// data, residual weights max(|r|, eps)^((p-2)/2) with its power, so the last
+// channel (log W_r in normalised units) becomes exp(y) * rms^wr_pow.
+__global__ void k_rescale_out(float* y, const float* rms, long long P, int C, int N, float wr_pow) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * C * N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)((i / P) % C);
+    const float r = rms[i / (P * C)];
+    y[i] = (c < C - 1) ? y[i] * r : expf(y[i]) * powf(r, wr_pow);
+  }
+}
+
+// Training targets in normalised units from a solve's model m [N][C-1][P] and
+// final residual weights wr [N][P]: t = m / rms, log(wr) - wr_pow log(rms).
+__global__ void k_targets(const float* m, const float* wr, const float* rms, float* t,
+                          long long P, int C, int N, float wr_pow) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * C * N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i % P;
+    const int c = (int)((i / P) % C);
+    const long long n = i / (P * C);
+    const float r = rms[n];
+    t[i] = (c < C - 1) ? m[(n * (C - 1) + c) * P + p] / r
+                       : logf(fmaxf(wr[n * P + p], 1e-30f)) - wr_pow * logf(r);
+  }
+}
+
+// The warm start in input units: m0 [N][C-1][P] and wr0 [N][P] from the NHWC head output.
+__global__ void k_predict_out(const float* y, const float* rms, float* m0, float* wr0,
+                              long long P, int C, int N, float wr_pow) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * C * N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i % P;
+    const int c = (int)((i / P) % C);
+    const long long n = i / (P * C);
+    const float r = rms[n];
+    const float v = y[(n * P + p) * C + c];
+    if (c < C - 1) {
+      if (m0) m0[(n * (C - 1) + c) * P + p] = v * r;
+    } else if (wr0) {
+      wr0[n * P + p] = expf(v) * powf(r, wr_pow);
+    }
+  }
+}
+
+// -------------------------------------------------------------------------
+struct Layer {
+  int ci, co, k;
+  long long w_off, b_off;   // into the flat parameter buffer
+  bf16 *wf = nullptr, *wt = nullptr;
+};
+
+int grid1d(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+using namespace ashrt;
+
+struct ashrt_unet {
+  int H = 0, W = 0, cout = 0, maxb = 0;
+  int ch[4] = {16, 48, 96, 192};
+  std::vector<Layer> L;              // 15 layers, reference order
+  long long nparam = 0;
+  float *w = nullptr, *g = nullptr, *am = nullptr, *av = nullptr;   // master, grad, Adam
+  long long adam_t = 0;
+  // activations (bf16) and gradients (fp32)
+  std::vector<void*> allocs;
+  bf16 *x, *e1a, *cat1, *p1, *e2a, *cat2, *p2, *e3a, *cat3, *p3, *ba, *bb, *d3a, *d3b, *d2a, *d2b,
+      *d1a, *d1b;
+  float *y, *gy, *g1a, *gcat1, *gp1, *g2a, *gcat2, *gp2, *g3a, *gcat3, *gp3, *gba, *gbb, *gd3a,
+      *gd3b, *gd2a, *gd2b, *gd1a, *gd1b;
+  float *rms, *lam;
+  double* loss;
+  std::vector<float> lam_h;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(ashrt_unet* u, T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
+  if (e == cudaSuccess) u->allocs.push_back(*p);
+  return e;
+}
+
+Tensor T_(void* p, int ps, int off = 0) {
+  Tensor t;
+  t.p = p;
+  t.ps = ps;
+  t.off = off;
+  return t;
+}
+
+template <int K, typename TI, typename TO>
+void conv(Tensor in, Tensor mask, const bf16* w, const float* bias, Tensor out, int N, int H,
+          int W, int Cin, int Cout, int relu, cudaStream_t s) {
+  ConvArgs a;
+  a.in = in;
+  a.mask = mask;
+  a.w = w;
+  a.bias = bias;
+  a.out = out;
+  a.N = N;
+  a.H = H;
+  a.W = W;
+  a.Cin = Cin;
+  a.Cout = Cout;
+  a.relu = relu;
+  dim3 grid((unsigned)((long long)N * H * ((W + kPix - 1) / kPix)), (Cout + kCh - 1) / kCh);
+  k_conv<K, TI, TO><<<grid, kPix, 0, s>>>(a);
+  count_launches(1);
+}
+
+template <int K>
+void wgrad(Tensor in, Tensor g, Tensor mask, float* gw, float* gb, int N, int H, int W, int Cin,
+           int Cout, cudaStream_t s) {
+  WgradArgs a;
+  a.in = in;
+  a.g = g;
+  a.mask = mask;
+  a.gw = gw;
+  a.gb = gb;
+  a.N = N;
+  a.H = H;
+  a.W = W;
+  a.Cin = Cin;
+  a.Cout = Cout;
+  const int xt = (W + kPix - 1) / kPix;
+  const long long ch_tiles = (long long)((Cin + kCh - 1) / kCh) * ((Cout + kCh - 1) / kCh);
+  const long long want_strips = (152LL * 8 + ch_tiles - 1) / ch_tiles;   // ~8 CTAs per SM
+  const long long rows = (long long)N * H;
+  long long strips_per_col = (want_strips + xt - 1) / xt;
+  if (strips_per_col > rows) strips_per_col = rows;
+  if (strips_per_col < 1) strips_per_col = 1;
+  a.rows_per = (int)((rows + strips_per_col - 1) / strips_per_col);
+  const long long nstrip = (rows + a.rows_per - 1) / a.rows_per;
+  dim3 grid((unsigned)(nstrip * xt), (Cin + kCh - 1) / kCh, (Cout + kCh - 1) / kCh);
+  k_wgrad<K><<<grid, 256, 0, s>>>(a);
+  count_launches(1);
+}
+
+// Forward pass on `n` images already packed in u->x; writes u->y (NHWC fp32).
+void net_forward(ashrt_unet* u, int n, cudaStream_t s) {
+  const int H = u->H, W = u->W, c0 = u->ch[0], c1 = u->ch[1], c2 = u->ch[2], c3 = u->ch[3];
+  const Tensor none = T_(nullptr, 0);
+  auto& L = u->L;
+  auto B = [&](int i) { return u->w + L[i].b_off; };
+  auto grid = [&](long long cnt) { return grid1d(cnt); };
+  // encoder
+  conv<3, bf16, bf16>(T_(u->x, 1), none, L[0].wf, B(0), T_(u->e1a, c0), n, H, W, 1, c0, 1, s);
+  conv<3, bf16, bf16>(T_(u->e1a, c0), none, L[1].wf, B(1), T_(u->cat1, c1 + c0, c1), n, H, W, c0, c0, 1, s);
+  k_pool<<<grid((long long)n * H * W / 4 * c0), 256, 0, s>>>(T_(u->cat1, c1 + c0, c1), T_(u->p1, c0), n, H, W, c0);
+  conv<3, bf16, bf16>(T_(u->p1, c0), none, L[2].wf, B(2), T_(u->e2a, c1), n, H / 2, W / 2, c0, c1, 1, s);
+  conv<3, bf16, bf16>(T_(u->e2a, c1), none, L[3].wf, B(3), T_(u->cat2, c2 + c1, c2), n, H / 2, W / 2, c1, c1, 1, s);
+  k_pool<<<grid((long long)n * H * W / 16 * c1), 256, 0, s>>>(T_(u->cat2, c2 + c1, c2), T_(u->p2, c1), n, H / 2, W / 2, c1);
+  conv<3, bf16, bf16>(T_(u->p2, c1), none, L[4].wf, B(4), T_(u->e3a, c2), n, H / 4, W / 4, c1, c2, 1, s);
+  conv<3, bf16, bf16>(T_(u->e3a, c2), none, L[5].wf, B(5), T_(u->cat3, c3 + c2, c3), n, H / 4, W / 4, c2, c2, 1, s);
+  k_pool<<<grid((long long)n * H * W / 64 * c2), 256, 0, s>>>(T_(u->cat3, c3 + c2, c3), T_(u->p3, c2), n, H / 4, W / 4, c2);
+  conv<3, bf16, bf16>(T_(u->p3, c2), none, L[6].wf, B(6), T_(u->ba, c3), n, H / 8, W / 8, c2, c3, 1, s);
+  conv<3, bf16, bf16>(T_(u->ba, c3), none, L[7].wf, B(7), T_(u->bb, c3), n, H / 8, W / 8, c3, c3, 1, s);
+  // decoder
+  k_up<<<grid((long long)n * H * W / 16 * c3), 256, 0, s>>>(T_(u->bb, c3), T_(u->cat3, c3 + c2, 0), n, H / 4, W / 4, c3);
+  conv<3, bf16, bf16>(T_(u->cat3, c3 + c2), none, L[8].wf, B(8), T_(u->d3a, c2), n, H / 4, W / 4, c3 + c2, c2, 1, s);
+  conv<3, bf16, bf16>(T_(u->d3a, c2), none, L[9].wf, B(9), T_(u->d3b, c2), n, H / 4, W / 4, c2, c2, 1, s);
+  k_up<<<grid((long long)n * H * W / 4 * c2), 256, 0, s>>>(T_(u->d3b, c2), T_(u->cat2, c2 + c1, 0), n, H / 2, W / 2, c2);
+  conv<3, bf16, bf16>(T_(u->cat2, c2 + c1), none, L[10].wf, B(10), T_(u->d2a, c1), n, H / 2, W / 2, c2 + c1, c1, 1, s);
+  conv<3, bf16, bf16>(T_(u->d2a, c1), none, L[11].wf, B(11), T_(u->d2b, c1), n, H / 2, W / 2, c1, c1, 1, s);
+  k_up<<<grid((long long)n * H * W * c1), 256, 0, s>>>(T_(u->d2b, c1), T_(u->cat1, c1 + c0, 0), n, H, W, c1);
+  conv<3, bf16, bf16>(T_(u->cat1, c1 + c0), none, L[12].wf, B(12), T_(u->d1a, c0), n, H, W, c1 + c0, c0, 1, s);
+  conv<3, bf16, bf16>(T_(u->d1a, c0), none, L[13].wf, B(13), T_(u->d1b, c0), n, H, W, c0, c0, 1, s);
+  conv<1, bf16, float>(T_(u->d1b, c0), none, L[14].wf, B(14), T_(u->y, u->cout), n, H, W, c0, u->cout, 0, s);
+  count_launches(6);
+}
+
+// Backward pass from u->gy (NHWC fp32); accumulates parameter gradients in u->g.
+void net_backward(ashrt_unet* u, int n, cudaStream_t s) {
+  const int H = u->H, W = u->W, c0 = u->ch[0], c1 = u->ch[1], c2 = u->ch[2], c3 = u->ch[3];
+  const Tensor none = T_(nullptr, 0);
+  auto& L = u->L;
+  auto GW = [&](int i) { return u->g + L[i].w_off; };
+  auto GB = [&](int i) { return u->g + L[i].b_off; };
+  auto grid = [&](long long cnt) { return grid1d(cnt); };
+  // Each conv layer i maps (input tensor in_i) -> (output act_i); given the
+  // gradient G of its output (masked by act_i > 0 when it has a ReLU):
+  //   wgrad(in_i, G, mask act_i) and, unless it is the first layer,
+  //   G_in = conv(G masked, flipped weights).
+  // head (no ReLU)
+  wgrad<1>(T_(u->d1b, c0), T_(u->gy, u->cout), none, GW(14), GB(14), n, H, W, c0, u->cout, s);
+  conv<1, float, float>(T_(u->gy, u->cout), none, L[14].wt, nullptr, T_(u->gd1b, c0), n, H, W, u->cout, c0, 0, s);
+  // dec1
+  wgrad<3>(T_(u->d1a, c0), T_(u->gd1b, c0), T_(u->d1b, c0), GW(13), GB(13), n, H, W, c0, c0, s);
+  conv<3, float, float>(T_(u->gd1b, c0), T_(u->d1b, c0), L[13].wt, nullptr, T_(u->gd1a, c0), n, H, W, c0, c0, 0, s);
+  wgrad<3>(T_(u->cat1, c1 + c0), T_(u->gd1a, c0), T_(u->d1a, c0), GW(12), GB(12), n, H, W, c1 + c0, c0, s);
+  conv<3, float, float>(T_(u->gd1a, c0), T_(u->d1a, c0), L[12].wt, nullptr, T_(u->gcat1, c1 + c0), n, H, W, c0, c1 + c0, 0, s);
+  k_up_bwd<<<grid((long long)n * H * W / 4 * c1), 256, 0, s>>>(T_(u->gcat1, c1 + c0, 0), T_(u->gd2b, c1), n, H / 2, W / 2, c1);
+  // dec2
+  wgrad<3>(T_(u->d2a, c1), T_(u->gd2b, c1), T_(u->d2b, c1), GW(11), GB(11), n, H / 2, W / 2, c1, c1, s);
+  conv<3, float, float>(T_(u->gd2b, c1), T_(u->d2b, c1), L[11].wt, nullptr, T_(u->gd2a, c1), n, H / 2, W / 2, c1, c1, 0, s);
+  wgrad<3>(T_(u->cat2, c2 + c1), T_(u->gd2a, c1), T_(u->d2a, c1), GW(10), GB(10), n, H / 2, W / 2, c2 + c1, c1, s);
+  conv<3, float, float>(T_(u->gd2a, c1), T_(u->d2a, c1), L[10].wt, nullptr, T_(u->gcat2, c2 + c1), n, H / 2, W / 2, c1, c2 + c1, 0, s);
+  k_up_bwd<<<grid((long long)n * H * W / 16 * c2), 256, 0, s>>>(T_(u->gcat2, c2 + c1, 0), T_(u->gd3b, c2), n, H / 4, W / 4, c2);
+  // dec3
+  wgrad<3>(T_(u->d3a, c2), T_(u->gd3b, c2), T_(u->d3b, c2), GW(9), GB(9), n, H / 4, W / 4, c2, c2, s);
+  conv<3, float, float>(T_(u->gd3b, c2), T_(u->d3b, c2), L[9].wt, nullptr, T_(u->gd3a, c2), n, H / 4, W / 4, c2, c2, 0, s);
+  wgrad<3>(T_(u->cat3, c3 + c2), T_(u->gd3a, c2), T_(u->d3a, c2), GW(8), GB(8), n, H / 4, W / 4, c3 + c2, c2, s);
+  conv<3, float, float>(T_(u->gd3a, c2), T_(u->d3a, c2), L[8].wt, nullptr, T_(u->gcat3, c3 + c2), n, H / 4, W / 4, c2, c3 + c2, 0, s);
+  k_up_bwd<<<grid((long long)n * H * W / 64 * c3), 256, 0, s>>>(T_(u->gcat3, c3 + c2, 0), T_(u->gbb, c3), n, H / 8, W / 8, c3);
+  // bottleneck
+  wgrad<3>(T_(u->ba, c3), T_(u->gbb, c3), T_(u->bb, c3), GW(7), GB(7), n, H / 8, W / 8, c3, c3, s);
+  conv<3, float, float>(T_(u->gbb, c3), T_(u->bb, c3), L[7].wt, nullptr, T_(u->gba, c3), n, H / 8, W / 8, c3, c3, 0, s);
+  wgrad<3>(T_(u->p3, c2), T_(u->gba, c3), T_(u->ba, c3), GW(6), GB(6), n, H / 8, W / 8, c2, c3, s);
+  conv<3, float, float>(T_(u->gba, c3), T_(u->ba, c3), L[6].wt, nullptr, T_(u->gp3, c2), n, H / 8, W / 8, c3, c2, 0, s);
+  k_pool_bwd_acc<<<grid((long long)n * H * W / 16 * c2), 256, 0, s>>>(T_(u->gp3, c2), T_(u->gcat3, c3 + c2, c3), n, H / 4, W / 4, c2);
+  // enc3 (its output s3 lives in cat3[c3:], gradient in gcat3[c3:])
+  wgrad<3>(T_(u->e3a, c2), T_(u->gcat3, c3 + c2, c3), T_(u->cat3, c3 + c2, c3), GW(5), GB(5), n, H / 4, W / 4, c2, c2, s);
+  conv<3, float, float>(T_(u->gcat3, c3 + c2, c3), T_(u->cat3, c3 + c2, c3), L[5].wt, nullptr, T_(u->g3a, c2), n, H / 4, W / 4, c2, c2, 0, s);
+  wgrad<3>(T_(u->p2, c1), T_(u->g3a, c2), T_(u->e3a, c2), GW(4), GB(4), n, H / 4, W / 4, c1, c2, s);
+  conv<3, float, float>(T_(u->g3a, c2), T_(u->e3a, c2), L[4].wt, nullptr, T_(u->gp2, c1), n, H / 4, W / 4, c2, c1, 0, s);
+  k_pool_bwd_acc<<<grid((long long)n * H * W / 4 * c1), 256, 0, s>>>(T_(u->gp2, c1), T_(u->gcat2, c2 + c1, c2), n, H / 2, W / 2, c1);
+  // enc2
+  wgrad<3>(T_(u->e2a, c1), T_(u->gcat2, c2 + c1, c2), T_(u->cat2, c2 + c1, c2), GW(3), GB(3), n, H / 2, W / 2, c1, c1, s);
+  conv<3, float, float>(T_(u->gcat2, c2 + c1, c2), T_(u->cat2, c2 + c1, c2), L[3].wt, nullptr, T_(u->g2a, c1), n, H / 2, W / 2, c1, c1, 0, s);
+  wgrad<3>(T_(u->p1, c0), T_(u->g2a, c1), T_(u->e2a, c1), GW(2), GB(2), n, H / 2, W / 2, c0, c1, s);
+  conv<3, float, float>(T_(u->g2a, c1), T_(u->e2a, c1), L[2].wt, nullptr, T_(u->gp1, c0), n, H / 2, W / 2, c1, c0, 0, s);
+  k_pool_bwd_acc<<<grid((long long)n * H * W * c0), 256, 0, s>>>(T_(u->gp1, c0), T_(u->gcat1, c1 + c0, c1), n, H, W, c0);
+  // enc1
+  wgrad<3>(T_(u->e1a, c0), T_(u->gcat1, c1 + c0, c1), T_(u->cat1, c1 + c0, c1), GW(1), GB(1), n, H, W, c0, c0, s);
+  conv<3, float, float>(T_(u->gcat1, c1 + c0, c1), T_(u->cat1, c1 + c0, c1), L[1].wt, nullptr, T_(u->g1a, c0), n, H, W, c0, c0, 0, s);
+  wgrad<3>(T_(u->x, 1), T_(u->g1a, c0), T_(u->e1a, c0), GW(0), GB(0), n, H, W, 1, c0, s);
+  count_launches(6);
+}
+
+cudaError_t refresh_bf16_weights(ashrt_unet* u, cudaStream_t s) {
+  for (auto& l : u->L) {
+    const int total = l.co * l.ci * l.k * l.k;
+    k_wconv<<<(total + 255) / 256, 256, 0, s>>>(u->w + l.w_off, l.wf, l.wt, l.co, l.ci, l.k);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+ashrt_status ashrt_unet_create(ashrt_unet** out, int H, int W, int out_channels, int max_batch,
+                               const float* init_params, long long n_init) {
+  if (!out || H < 8 || W < 8 || H % 8 || W % 8 || out_channels < 1 || max_batch < 1) {
+    set_error("ashrt_unet_create: need H, W multiples of 8 (>= 8), out_channels >= 1, max_batch >= 1");
+    return ASHRT_EINVAL;
+  }
+  *out = nullptr;
+  ashrt_unet* u = new ashrt_unet();
+  u->H = H;
+  u->W = W;
+  u->cout = out_channels;
+  u->maxb = max_batch;
+  const int c0 = u->ch[0], c1 = u->ch[1], c2 = u->ch[2], c3 = u->ch[3];
+  const int spec[15][3] = {{1, c0, 3},       {c0, c0, 3},      {c0, c1, 3}, {c1, c1, 3},
+                           {c1, c2, 3},      {c2, c2, 3},      {c2, c3, 3}, {c3, c3, 3},
+                           {c3 + c2, c2, 3}, {c2, c2, 3},      {c2 + c1, c1, 3}, {c1, c1, 3},
+                           {c1 + c0, c0, 3}, {c0, c0, 3},      {c0, out_channels, 1}};
+  long long off = 0;
+  for (auto& sp : spec) {
+    Layer l;
+    l.ci = sp[0];
+    l.co = sp[1];
+    l.k = sp[2];
+    l.w_off = off;
+    off += (long long)l.co * l.ci * l.k * l.k;
+    l.b_off = off;
+    off += l.co;
+    u->L.push_back(l);
+  }
+  u->nparam = off;
+  const long long P0 = (long long)max_batch * H * W;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t n) {
+    if (e == cudaSuccess) e = dalloc(u, p, n);
+  };
+  A(&u->w, off);
+  A(&u->g, off);
+  A(&u->am, off);
+  A(&u->av, off);
+  for (auto& l : u->L) {
+    A(&l.wf, (size_t)l.co * l.ci * l.k * l.k);
+    A(&l.wt, (size_t)l.co * l.ci * l.k * l.k);
+  }
+  A(&u->x, P0);
+  A(&u->e1a, P0 * c0);
+  A(&u->cat1, P0 * (c1 + c0));
+  A(&u->p1, P0 / 4 * c0);
+  A(&u->e2a, P0 / 4 * c1);
+  A(&u->cat2, P0 / 4 * (c2 + c1));
+  A(&u->p2, P0 / 16 * c1);
+  A(&u->e3a, P0 / 16 * c2);
+  A(&u->cat3, P0 / 16 * (c3 + c2));
+  A(&u->p3, P0 / 64 * c2);
+  A(&u->ba, P0 / 64 * c3);
+  A(&u->bb, P0 / 64 * c3);
+  A(&u->d3a, P0 / 16 * c2);
+  A(&u->d3b, P0 / 16 * c2);
+  A(&u->d2a, P0 / 4 * c1);
+  A(&u->d2b, P0 / 4 * c1);
+  A(&u->d1a, P0 * c0);
+  A(&u->d1b, P0 * c0);
+  A(&u->y, P0 * out_channels);
+  A(&u->gy, P0 * out_channels);
+  A(&u->g1a, P0 * c0);
+  A(&u->gcat1, P0 * (c1 + c0));
+  A(&u->gp1, P0 / 4 * c0);
+  A(&u->g2a, P0 / 4 * c1);
+  A(&u->gcat2, P0 / 4 * (c2 + c1));
+  A(&u->gp2, P0 / 16 * c1);
+  A(&u->g3a, P0 / 16 * c2);
+  A(&u->gcat3, P0 / 16 * (c3 + c2));
+  A(&u->gp3, P0 / 64 * c2);
+  A(&u->gba, P0 / 64 * c3);
+  A(&u->gbb, P0 / 64 * c3);
+  A(&u->gd3a, P0 / 16 * c2);
+  A(&u->gd3b, P0 / 16 * c2);
+  A(&u->gd2a, P0 / 4 * c1);
+  A(&u->gd2b, P0 / 4 * c1);
+  A(&u->gd1a, P0 * c0);
+  A(&u->gd1b, P0 * c0);
+  A(&u->rms, max_batch);
+  A(&u->lam, out_channels);
+  A(&u->loss, 1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("ashrt_unet_create: cudaMalloc failed: %s", cudaGetErrorString(e));
+    for (void* p : u->allocs) cudaFree(p);
+    delete u;
+    return ASHRT_ENOMEM;
+  }
+  // parameters: given, or He-normal from a fixed-seed generator (host, Box-Muller)
+  std::vector<float> h(off, 0.f);
+  if (init_params) {
+    if (n_init != off) {
+      set_error("ashrt_unet_create: %lld initial parameters given, the network has %lld", n_init, off);
+      for (void* p : u->allocs) cudaFree(p);
+      delete u;
+      return ASHRT_EINVAL;
+    }
+    for (long long i = 0; i < off; ++i) h[i] = init_params[i];
+  } else {
+    uint64_t st = 0x9e3779b97f4a7c15ull;
+    auto uni = [&]() {
+      st ^= st << 13;
+      st ^= st >> 7;
+      st ^= st << 17;
+      return ((st >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    for (auto& l : u->L) {
+      const double sd = std::sqrt(2.0 / (l.ci * l.k * l.k));
+      for (long long i = 0; i < (long long)l.co * l.ci * l.k * l.k; ++i) {
+        const double a = uni(), b = uni();
+        h[l.w_off + i] = (float)(sd * std::sqrt(-2.0 * std::log(a)) * std::cos(6.283185307179586 * b));
+      }
+    }
+  }
+  e = cudaMemcpy(u->w, h.data(), off * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(u->am, 0, off * 4);
+  if (e == cudaSuccess) e = cudaMemset(u->av, 0, off * 4);
+  if (e == cudaSuccess) e = cudaMemset(u->g, 0, off * 4);
+  if (e == cudaSuccess) e = refresh_bf16_weights(u, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_error("ashrt_unet_create: init failed: %s", cudaGetErrorString(e));
+    for (void* p : u->allocs) cudaFree(p);
+    delete u;
+    return ASHRT_ECUDA;
+  }
+  u->lam_h.assign(out_channels, 1.f);
+  cudaMemcpy(u->lam, u->lam_h.data(), out_channels * 4, cudaMemcpyHostToDevice);
+  *out = u;
+  return ASHRT_OK;
+}
+
+void ashrt_unet_destroy(ashrt_unet* u) {
+  if (!u) return;
+  cudaDeviceSynchronize();
+  for (void* p : u->allocs) cudaFree(p);
+  delete u;
+}
+
+long long ashrt_unet_param_count(const ashrt_unet* u) { return u ? u->nparam : 0; }
+
+ashrt_status ashrt_unet_get(const ashrt_unet* u, float* params, float* grads, long long n) {
+  if (!u || n != u->nparam) {
+    set_error("ashrt_unet_get: NULL network or wrong count");
+    return ASHRT_EINVAL;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && params) e = cudaMemcpy(params, u->w, n * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && grads) e = cudaMemcpy(grads, u->g, n * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_error("ashrt_unet_get: %s", cudaGetErrorString(e));
+    return ASHRT_ECUDA;
+  }
+  return ASHRT_OK;
+}
+
+// x: [n][H][W] fp32 inputs (gathers [nx][nt]); y: [n][cout][H][W] fp32 outputs.
+// Inputs are scaled by their RMS; with `rescale` the outputs are returned in
+// input units for an IRLS misfit power p: channels < cout-1 multiplied by the
+// RMS (model panels), the last channel as exp(y) * RMS^((p-2)/2) (residual
+// weights).
+ashrt_status ashrt_unet_forward(ashrt_unet* u, const float* x, float* y, int n, int rescale,
+                                float p, void* stream) {
+  if (!u || !x || !y || n < 1 || n > u->maxb) {
+    set_error("ashrt_unet_forward: NULL argument or n outside [1, max_batch]");
+    return ASHRT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long per = (long long)u->H * u->W;
+  k_rms<<<n, 256, 0, s>>>(x, per, u->rms);
+  k_pack_in<<<grid1d(per * n), 256, 0, s>>>(x, u->rms, u->x, per, n);
+  count_launches(2);
+  net_forward(u, n, s);
+  k_unpack_out<<<grid1d(per * u->cout * n), 256, 0, s>>>(u->y, y, per, u->cout, n);
+  count_launches(1);
+  if (rescale) {
+    k_rescale_out<<<grid1d(per * u->cout * n), 256, 0, s>>>(y, u->rms, per, u->cout, n,
+                                                           0.5f * (p - 2.f));
+    count_launches(1);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("ashrt_unet_forward: %s", cudaGetErrorString(e));
+    return ASHRT_ECUDA;
+  }
+  return ASHRT_OK;
+}
+
+// One training step on n pairs: x [n][H][W], target [n][cout][H][W] (targets
+// in the network's normalised units), per-channel loss weights (host, cout
+// values, or NULL = 1).  Adam with the given learning rate; returns the loss.
+ashrt_status ashrt_unet_train_step(ashrt_unet* u, const float* x, const float* target, int n,
+                                   const float* channel_weight, float lr, double* loss_out,
+                                   void* stream) {
+  if (!u || !x || !target || n < 1 || n > u->maxb) {
+    set_error("ashrt_unet_train_step: NULL argument or n outside [1, max_batch]");
+    return ASHRT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long per = (long long)u->H * u->W;
+  if (channel_weight) {
+    bool same = true;
+    for (int c = 0; c < u->cout; ++c) same = same && (u->lam_h[c] == channel_weight[c]);
+    if (!same) {
+      u->lam_h.assign(channel_weight, channel_weight + u->cout);
+      cudaMemcpyAsync(u->lam, u->lam_h.data(), u->cout * 4, cudaMemcpyHostToDevice, s);
+    }
+  }
+  cudaMemsetAsync(u->loss, 0, sizeof(double), s);
+  cudaMemsetAsync(u->g, 0, u->nparam * 4, s);
+  k_rms<<<n, 256, 0, s>>>(x, per, u->rms);
+  k_pack_in<<<grid1d(per * n), 256, 0, s>>>(x, u->rms, u->x, per, n);
+  count_launches(2);
+  net_forward(u, n, s);
+  k_mse<<<grid1d(per * u->cout * n), 256, 0, s>>>(u->y, target, u->lam, u->gy, per, u->cout, n,
+                                                  u->loss);
+  count_launches(1);
+  net_backward(u, n, s);
+  if (lr > 0.f) {
+    u->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)u->adam_t);
+    const float c2 = 1.f - std::pow(b2, (float)u->adam_t);
+    k_adam<<<grid1d(u->nparam), 256, 0, s>>>(u->w, u->g, u->am, u->av, u->nparam, lr, b1, b2,
+                                            1e-8f, c1, c2);
+    count_launches(1);
+    refresh_bf16_weights(u, s);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && loss_out) {
+    e = cudaMemcpyAsync(loss_out, u->loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) {
+    set_error("ashrt_unet_train_step: %s", cudaGetErrorString(e));
+    return ASHRT_ECUDA;
+  }
+  return ASHRT_OK;
+}
+
+ashrt_status ashrt_unet_targets(ashrt_unet* u, const float* x, const float* m, const float* wr,
+                                float* t, int n, float p, void* stream) {
+  if (!u || !x || !m || !wr || !t || n < 1 || n > u->maxb) {
+    set_error("ashrt_unet_targets: NULL argument or n outside [1, max_batch]");
+    return ASHRT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long per = (long long)u->H * u->W;
+  k_rms<<<n, 256, 0, s>>>(x, per, u->rms);
+  k_targets<<<grid1d(per * u->cout * n), 256, 0, s>>>(m, wr, u->rms, t, per, u->cout, n,
+                                                      0.5f * (p - 2.f));
+  count_launches(2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("ashrt_unet_targets: %s", cudaGetErrorString(e));
+    return ASHRT_ECUDA;
+  }
+  return ASHRT_OK;
+}
+
+ashrt_status ashrt_unet_predict(ashrt_unet* u, const float* x, float* m0, float* wr0, int n,
+                                float p, void* stream) {
+  if (!u || !x || (!m0 && !wr0) || n < 1 || n > u->maxb) {
+    set_error("ashrt_unet_predict: NULL argument or n outside [1, max_batch]");
+    return ASHRT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long per = (long long)u->H * u->W;
+  k_rms<<<n, 256, 0, s>>>(x, per, u->rms);
+  k_pack_in<<<grid1d(per * n), 256, 0, s>>>(x, u->rms, u->x, per, n);
+  count_launches(2);
+  net_forward(u, n, s);
+  k_predict_out<<<grid1d(per * u->cout * n), 256, 0, s>>>(u->y, u->rms, m0, wr0, per, u->cout,
+                                                          n, 0.5f * (p - 2.f));
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("ashrt_unet_predict: %s", cudaGetErrorString(e));
+    return ASHRT_ECUDA;
+  }
+  return ASHRT_OK;
+}
+
+}  // extern "C"
+

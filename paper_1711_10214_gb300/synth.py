@@ -21,6 +21,11 @@ Config recipes (seed = 1000 * config + gather):
       traces removed.  Scan: 24 velocities x 16 asymptote shifts.
   c4  uneven gathers, nx ~ U{96..480}, nt 1500; 5-40 events; 3 interfering
       sources with delays ~ U[0,1.5] s.  Scan: 24 velocities.
+  c5  warm-start training and evaluation gathers, nt 1024, nx 256: the c3
+      signal (5 reflections + 40 diffractions, tau0 ~ U[0,0.4] s) blended as
+      in c2 (2 interfering sources of 5 events, delays ~ U[0,1] s, peak
+      ratio ~ U[1,10]).  Scan: 24 velocities, tau0 = {0}.  Smaller nt / nx
+      keep the recipe with the time ranges clipped to the record.
 """
 import numpy as np
 
@@ -145,6 +150,44 @@ def config3(n_gathers=16, nt=1024, nx=256, nv=24, nt0=16, keep=0.5):
     return dict(nt=nt, nx=nx, dt=DT, dx=DX, clean=clean, observed=observed, mask=mask,
                 velocities=velocity_scan(1400.0, 3500.0, nv),
                 t0s=np.linspace(0.0, 0.4, nt0).astype(np.float32), f_peak=25.0)
+
+
+def config5_gather(g, nt=1024, nx=256):
+    """c5 gather g: (clean, pseudo-deblended), both [nx][nt]."""
+    rng = rng_for(5, g)
+    return _gather(rng, nt, nx, 5, (0.2, min(3.0, 0.75 * nt * DT)), (1400.0, 3500.0), 25.0,
+                   2, min(1.0, 0.25 * nt * DT), (1.0, 10.0), diffr=40, t0_range=(0.0, 0.4))
+
+
+def _c5_job(args):
+    g, nt, nx = args
+    return config5_gather(g, nt, nx)
+
+
+def _c1_job(args):
+    c = config1(args[0])
+    return c["clean"], c["blended"]
+
+
+def config5(gathers, nt=1024, nx=256, processes=0):
+    """c5 gathers for the seeds in `gathers`: dict with clean / blended
+    [len][nx][nt] (float32), velocities and t0s.  processes > 1 renders them
+    in a pool of that many 'spawn' workers."""
+    gathers = list(gathers)
+    clean = np.zeros((len(gathers), nx, nt), np.float32)
+    blended = np.zeros_like(clean)
+    jobs = [(g, nt, nx) for g in gathers]
+    if processes and processes > 1 and len(gathers) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            res = pool.map(_c5_job, jobs, chunksize=max(1, len(jobs) // (4 * processes)))
+    else:
+        res = [_c5_job(j) for j in jobs]
+    for i, (c, b) in enumerate(res):
+        clean[i], blended[i] = c, b
+    return dict(nt=nt, nx=nx, dt=DT, dx=DX, clean=clean, blended=blended,
+                velocities=velocity_scan(1400.0, 3500.0, 24), t0s=np.zeros(1, np.float32),
+                f_peak=25.0)
 
 
 def config4_sizes(n_gathers=2000):

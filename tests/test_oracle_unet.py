@@ -65,3 +65,37 @@ def test_adam_first_step_moves_by_lr():
     g = {"w": np.array([0.3, -5.0])}
     unet.adam_step(p, g, {}, lr=0.01)
     np.testing.assert_allclose(p["w"], [0.99, -1.99], atol=1e-7)
+
+
+def test_bf16_round_matches_torch_and_ties_to_even():
+    """bfloat16 rounding against torch's CPU conversion, plus the exact cases:
+    representable values unchanged, halfway values to the even neighbour."""
+    import torch
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.integers(-20, 20, 2000),
+                        [0.0, -0.0, 1.0, -2.5, 3.0e38]])
+    x32 = x.astype(np.float32)
+    want = torch.from_numpy(x32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(unet.bf16_round(x32), want)
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to even -> 1
+    assert unet.bf16_round(1.0 + 2.0 ** -8) == 1.0
+    # 1 + 3 * 2^-8 is halfway between 1 + 2^-7 and 1 + 2^-6: -> 1 + 2^-6 (even)
+    assert unet.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    assert unet.bf16_round(1.0 + 2.0 ** -7) == 1.0 + 2.0 ** -7
+    assert unet.bf16_round(1.0 + 1.5 * 2.0 ** -8) == 1.0 + 2.0 ** -7
+
+
+def test_rounded_network_reduces_to_exact_on_representable_values():
+    """With weights, input and activations already bfloat16 values the
+    rounding model changes nothing but the activations the convolutions
+    create; with rnd = identity it is the exact network."""
+    rng = np.random.default_rng(6)
+    ch = (4, 6, 8, 10)
+    p = unet.init_params(rng, 1, 3, ch)
+    x = rng.standard_normal((1, 1, 16, 16))
+    y0, _ = unet.forward(p, x, 3, ch)
+    y1, _ = unet.forward(p, x, 3, ch, rnd=lambda v: v)
+    np.testing.assert_array_equal(y0, y1)
+    y2, _ = unet.forward(p, x, 3, ch, rnd=unet.bf16_round)
+    rel = np.linalg.norm(y2 - y0) / np.linalg.norm(y0)
+    assert 1e-5 < rel < 3e-2
