@@ -17,7 +17,7 @@ Follows ch. 4, "Robust Radon transform":
     mu = 0 by default, the CG count acting as the regulariser.
 Quality: Q = 10 log10(||d_o||^2 / ||d_o - d_r||^2)   (Eqs ch4_Qpd, ch4_Qr).
 
-Readings (listed in the design doc): W = I at the first outer iteration; CGLS is
+Readings where the thesis is silent: W = I at the first outer iteration; CGLS is
 warm-started from u0 = W_m m_prev; median of an even count is the mean of the
 two middle order statistics; MAD = 0 falls back to eps_r = 1e-6 max|r| (then
 1e-30); max|m| = 0 gives W_m = I; the misfit is J_k = sum |r_i|^p over the

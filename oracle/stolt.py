@@ -12,8 +12,7 @@ with the Stolt dispersion relation w_tau = sqrt(w^2 - (v k_x)^2) (ch. 5 and
 ch. 6, "modified dispersion relationship") and, optionally, the zero-phase
 wavelet C of ch. 4 ("L replaced by C L").
 
-Readings taken where the thesis is silent or inconsistent (each is listed in
-DESIGN.md):
+Readings taken where the thesis is silent or inconsistent:
   * analysis exp(-i), synthesis exp(+i); velocity enters as v (not v/2);
   * the T shift acts on the data frequency w: forward exp(-i w tau0);
   * M is 2-tap linear interpolation along w at fixed k_x; the adjoint is the
