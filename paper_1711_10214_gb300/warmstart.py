@@ -63,7 +63,7 @@ class WarmStart:
     """A plan with the solver plus a U-Net for one gather size."""
 
     def __init__(self, nt, nx, velocities, dt=synth.DT, dx=synth.DX, chunk=64, train_batch=8,
-                 wavelet_peak_hz=25.0, p=1.0, q=1.0, params=None, source=None, w_weight=0.5):
+                 wavelet_peak_hz=25.0, p=1.0, q=1.0, params=None, source=None, w_weight=0.75):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda:0")
@@ -239,13 +239,13 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=1)
     ap.add_argument("--nt", type=int, default=1024)
     ap.add_argument("--nx", type=int, default=256)
-    ap.add_argument("--train", type=int, default=4096)
-    ap.add_argument("--test", type=int, default=128)
-    ap.add_argument("--passes", type=int, default=2)
+    ap.add_argument("--train", type=int, default=2048)
+    ap.add_argument("--test", type=int, default=64)
+    ap.add_argument("--passes", type=int, default=6)
     ap.add_argument("--chunk", type=int, default=64)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--w-weight", type=float, default=0.5)
+    ap.add_argument("--w-weight", type=float, default=0.75)
     ap.add_argument("--processes", type=int, default=min(12, os.cpu_count() or 1))
     ap.add_argument("--out", default=None)
     ap.add_argument("--save-params", default=None)
