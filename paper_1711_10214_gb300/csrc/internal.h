@@ -43,6 +43,8 @@ struct RowArgs {
   const float2* acone = nullptr;   // [nv][Lh] cone parameter a as (hi, lo) floats
   const unsigned* taps = nullptr;  // [nv][Lh][taps_ld] Stolt taps of |k| (see tap_word)
   int taps_ld = 0;                 // words per (v, l) row: Nt/2 + 1 rounded up to 4
+  const unsigned short* ks = nullptr;  // [nv][Lh][ks_ld] adjoint run starts (see build_ks_rows)
+  int ks_ld = 0;                       // entries per (v, l) row: Nt/2 + 2 rounded up to 8
   const float2* phase = nullptr;   // [nt0][Nt] exp(-i w tau0), or null (tau0 == 0)
   int batch = 0;
   int minb = 3;                    // register-cap variant (resident CTAs per SM): 1, 2, 3
@@ -61,6 +63,13 @@ constexpr unsigned kTapInvalid = 0xffffffffu;
 inline int taps_row_len(int Nt) { return ((Nt / 2 + 1) + 3) & ~3; }
 void build_tap_rows(const float* velocities, int nv, int Nt, int Nx, int Lh, double dt, double dx,
                     unsigned* taps, int* kmin, float2* acone);
+// Run starts of the transposed map, one u16 row per (velocity, l): ks[J] is
+// the first |k| >= kmin whose tap floor index (word >> 20) is >= J, or Nt/2 if
+// none, for J in [0, Nt/2] (taken from the tap words, so both directions of
+// the map use the same indices).  Rows whose kmin >= Nt/2 are left 0.
+inline int ks_row_len(int Nt) { return ((Nt / 2 + 2) + 7) & ~7; }
+void build_ks_rows(const unsigned* taps, const int* kmin, int nv, int Lh, int Nt,
+                   unsigned short* ks);
 
 // Twiddle tables in the layout the device passes expect (see common.cuh).
 int twiddle_table_len(int logn);
@@ -118,6 +127,7 @@ struct ashrt_plan {
   int* kmin = nullptr;
   float2* acone = nullptr;
   unsigned* taps = nullptr;
+  unsigned short* ks = nullptr;
   float2* phase = nullptr;
   // workspace
   float2* X = nullptr;       // [max_batch][P][Lh][ld]

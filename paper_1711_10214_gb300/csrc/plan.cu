@@ -98,6 +98,23 @@ void build_tap_rows(const float* velocities, int nv, int Nt, int Nx, int Lh, dou
   }
 }
 
+void build_ks_rows(const unsigned* taps, const int* kmin, int nv, int Lh, int Nt,
+                   unsigned short* ks) {
+  const int H = Nt / 2, ldt = taps_row_len(Nt), ldk = ks_row_len(Nt);
+  for (size_t row = 0; row < (size_t)nv * Lh; ++row) {
+    unsigned short* r = ks + row * ldk;
+    for (int J = 0; J < ldk; ++J) r[J] = 0;
+    const int km = kmin[row];
+    if (km >= H) continue;
+    const unsigned* t = taps + row * ldt;
+    int k = km;
+    for (int J = 0; J <= H; ++J) {
+      while (k < H && (int)(t[k] >> 20) < J) ++k;
+      r[J] = (unsigned short)k;
+    }
+  }
+}
+
 static ashrt_status cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: %s", what, cudaGetErrorString(e));
   return ASHRT_ECUDA;
@@ -110,7 +127,7 @@ static ashrt_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 static void free_plan_memory(ashrt_plan* p) {
-  void* ptrs[] = {p->tw_t, p->tw_x, p->wt, p->kmin, p->acone, p->taps, p->phase, p->X, p->Y,
+  void* ptrs[] = {p->tw_t, p->tw_x, p->wt, p->kmin, p->acone, p->taps, p->ks, p->phase, p->X, p->Y,
                   p->u, p->pv, p->sv, p->wminv, p->r, p->qv, p->wr, p->y,
                   p->scal, p->sel, p->flags};
   for (void* q : ptrs)
@@ -254,6 +271,8 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
   ra.acone = p->acone;
   ra.taps = p->taps;
   ra.taps_ld = taps_row_len(p->Nt);
+  ra.ks = p->ks;
+  ra.ks_ld = ks_row_len(p->Nt);
   ra.phase = p->shift ? p->phase : nullptr;
   ra.batch = batch;
   ra.minb = p->rows_minb;
@@ -410,6 +429,8 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
   std::vector<float2> acone((size_t)nv * Lh);
   std::vector<unsigned> taps((size_t)nv * Lh * taps_row_len(Nt));
   build_tap_rows(velocities, nv, Nt, Nx, Lh, dt, dx, taps.data(), kmin.data(), acone.data());
+  std::vector<unsigned short> ks((size_t)nv * Lh * ks_row_len(Nt));
+  build_ks_rows(taps.data(), kmin.data(), nv, Lh, Nt, ks.data());
   // asymptote shift T: exp(-i w tau0), w = 2 pi kk / (Nt dt)
   std::vector<float2> phase((size_t)nt0 * Nt);
   bool shift = false;
@@ -438,6 +459,7 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
   chk(upload(&p->kmin, kmin, &total));
   chk(upload(&p->acone, acone, &total));
   chk(upload(&p->taps, taps, &total));
+  chk(upload(&p->ks, ks, &total));
   chk(upload(&p->phase, phase, &total));
   const size_t B = (size_t)p->max_batch;
   const size_t xpan = (size_t)Lh * p->ld;

@@ -41,11 +41,12 @@ namespace {
 // w_tau spectrum.  With J = |j|, bin j receives (1 - f) D(k) from every
 // source k on its side of the spectrum with floor(u(|k|)) = J and f D(k) from
 // every source with floor(u(|k|)) = J - 1 (bin 0 takes the primary taps of
-// both sides).  floor(u) is non-decreasing in |k|, so those sources are one
-// run of |k| starting at the first |k| with floor(u) >= J - 1: located from
-// the inverse |k| = sqrt(J^2 + a^2) and corrected on the staged tap row.
-// Every bin is written once, by its owner: no atomics, no clearing pass, and
-// the strided ownership spreads the bins outside the cone over all warps.
+// both sides).  floor(u) is non-decreasing in |k|, so with ks[J] = the first
+// |k| >= kmin whose floor(u) >= J (a host-built table row, staged with the
+// tap row) the sources of bin J are the run [ks[J-1], ks[J+1]): secondary
+// taps before ks[J], primary taps from it.  Every output bin is written once,
+// by its owner: no atomics, no clearing pass, and the strided ownership
+// spreads the bins outside the cone over all warps.
 template <int LOGN, bool SHIFT, int MINB>
 __global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
 stolt_adj_rows(RowArgs a) {
@@ -55,12 +56,16 @@ stolt_adj_rows(RowArgs a) {
   float4* buf = smem4;                          // per-panel w_tau spectrum, then its inverse FFT
   float4* dsp = smem4 + N;                      // data spectrum x W (both gathers)
   unsigned* stap = (unsigned*)(smem4 + 2 * N);  // tap row of the current panel
+  unsigned short* ks = (unsigned short*)(stap + a.taps_ld);   // run starts, [ks_ld]
   const int tid = threadIdx.x, l = blockIdx.x, b0 = 2 * blockIdx.y;
   const bool hasB = b0 + 1 < a.batch;
   const float2* yA = a.Y + (long long)b0 * a.y_batch + (long long)l * a.ld;
   const unsigned* trow = a.taps + (long long)l * a.taps_ld;
   const long long tstep = (long long)a.Lh * a.taps_ld;
+  const unsigned short* krow = a.ks + (long long)l * a.ks_ld;
+  const long long kstep = (long long)a.Lh * a.ks_ld;
   stage_taps(stap, trow, a.taps_ld, tid, T);
+  stage_u16(ks, krow, a.ks_ld, tid, T);
   cp_async_commit();
 
   float4 v[8];
@@ -80,8 +85,6 @@ stolt_adj_rows(RowArgs a) {
     cp_async_wait_all();
     __syncthreads();
     const int km = __ldg(a.kmin + iv * a.Lh + l);
-    const float2 ac = __ldg(a.acone + iv * a.Lh + l);
-    const float af = ac.x + ac.y;
     const float2* phj = SHIFT ? a.phase + (long long)jt * N : nullptr;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
@@ -90,32 +93,21 @@ stolt_adj_rows(RowArgs a) {
       if (j != H && km < H) {
         const bool pos = j < H;
         const int J = pos ? j : N - j;
-        // first |k| >= km with floor(u(|k|)) >= J - 1
-        int k = km;
-        if (J > 1) {
-          const float x = (float)(J - 1);
-          k = (int)ceilf(sqrtf(fmaf(x, x, af * af)));
-          k = min(max(k, km), H);
-          while (k > km && (int)(stap[k - 1] >> 20) >= J - 1) --k;
-          while (k < H && (int)(stap[k] >> 20) < J - 1) ++k;
-        }
-        for (; k < H; ++k) {
-          const unsigned w = stap[k];
-          const int b = (int)(w >> 20);
-          if (b > J) break;
-          const float f = (float)(w & 0xfffffu) * (1.0f / 1048576.0f);
+        const int kB = ks[J], kC = ks[J + 1];
+        const int kA = J > 0 ? (int)ks[J - 1] : kB;
+        for (int k = kA; k < kC; ++k) {
+          const float fr = (float)(stap[k] & 0xfffffu) * (1.0f / 1048576.0f);
           const int kn = pos ? k : N - k;
           float4 d = dsp[swz4(kn)];
           if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
-          if (b == J) {
-            if (J == 0) {                       // bin 0: primary taps of +k and -k
-              float4 dm = dsp[swz4(N - k)];
-              if (SHIFT) dm = cmul(dm, cconj(__ldg(phj + (N - k))));
-              d = cadd(d, dm);
-            }
-            acc = cfma(1.f - f, d, acc);
-          } else {                              // b == J - 1: secondary tap
-            acc = cfma(f, d, acc);
+          acc = cfma(k < kB ? fr : 1.f - fr, d, acc);
+        }
+        if (j == 0) {                            // bin 0 also takes the primary taps of -k
+          for (int k = kB; k < kC; ++k) {
+            const float fr = (float)(stap[k] & 0xfffffu) * (1.0f / 1048576.0f);
+            float4 d = dsp[swz4(N - k)];
+            if (SHIFT) d = cmul(d, cconj(__ldg(phj + (N - k))));
+            acc = cfma(1.f - fr, d, acc);
           }
         }
       }
@@ -125,6 +117,7 @@ stolt_adj_rows(RowArgs a) {
     if (p + 1 < a.P) {
       const int ivn = iv + 1 == a.nv ? 0 : iv + 1;
       stage_taps(stap, trow + ivn * tstep, a.taps_ld, tid, T);
+      stage_u16(ks, krow + ivn * kstep, a.ks_ld, tid, T);
       cp_async_commit();
     }
     row_pass_range<+1, LOGN, 0, S::NPASS - 1>(buf, a.tw, tid);
@@ -142,7 +135,8 @@ template <int LOGN, bool SHIFT, int MINB>
 cudaError_t launch_adj_v(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
-  const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.taps_ld * sizeof(unsigned);
+  const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.taps_ld * sizeof(unsigned) +
+                      (size_t)a.ks_ld * sizeof(unsigned short);
   cudaError_t e = set_smem(stolt_adj_rows<LOGN, SHIFT, MINB>, smem_cap<LOGN>(false), attr);
   if (e != cudaSuccess) return e;
   stolt_adj_rows<LOGN, SHIFT, MINB><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);

@@ -94,6 +94,11 @@ __device__ __forceinline__ void stage_taps(unsigned* dst, const unsigned* src, i
   for (int c = tid; c < (taps_ld >> 2); c += T) cp_async16(dst + 4 * c, src + 4 * c);
 }
 
+__device__ __forceinline__ void stage_u16(unsigned short* dst, const unsigned short* src, int n,
+                                          int tid, int T) {
+  for (int c = tid; c < (n >> 3); c += T) cp_async16(dst + 8 * c, src + 8 * c);
+}
+
 template <int N>
 __device__ __forceinline__ void load_pair(float4* v, const float2* __restrict__ rowA,
                                           const float2* __restrict__ rowB, int nt, int tid) {
@@ -116,6 +121,9 @@ inline cudaError_t set_smem(K kern, size_t bytes, bool& done) {
   return e;
 }
 
+// Shared bytes of the adjoint's run-start row (ks_row_len u16)
+inline constexpr size_t adj_ks_bytes(int N) { return (size_t)(((N / 2 + 2) + 7) & ~7) * 2; }
+
 // Largest dynamic shared memory a launch of the LOGN kernels may request
 // (ld <= Nt, taps row <= Nt/2 + 4 words): the attribute is set once to it.
 template <int LOGN>
@@ -123,7 +131,7 @@ inline size_t smem_cap(bool fwd) {
   constexpr int N = 1 << LOGN;
   const size_t taps = (size_t)(N / 2 + 4) * sizeof(unsigned);
   return fwd ? (size_t)N * sizeof(float4) + (size_t)2 * N * sizeof(float2) + 2 * taps
-             : (size_t)2 * N * sizeof(float4) + taps;
+             : (size_t)2 * N * sizeof(float4) + taps + adj_ks_bytes(N);
 }
 
 inline int row_log2(int n) {
