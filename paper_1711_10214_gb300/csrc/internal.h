@@ -27,6 +27,25 @@ struct XfftArgs {
   const float2* tw = nullptr;        // base twiddles of length Nx
   int slabs = 0;
   int cols = 16;                     // complex time columns per CTA: 16 or 8 (Nx <= 512)
+  // r2c only: a CGLS vector update fused into the input load (the solver's
+  // mu = 0 path).  Per gather g, coef[g] = (cs, beta, alpha, -):
+  //   mode 1 (model side): x = cs s + beta p; p <- x; u <- u + alpha p_old
+  //   mode 2 (data side):  x = r - alpha q;  r <- x
+  // where p (mode 1) or r (mode 2) is in_real, read and written in place,
+  // and x is then transformed.
+  int cg_mode = 0;
+  float* cg_io = nullptr;            // == in_real, written
+  const float* cg_s = nullptr;       // s (mode 1) or q (mode 2)
+  float* cg_u = nullptr;             // u (mode 1)
+  const float4* cg_coef = nullptr;   // [gathers]
+};
+
+// A CGLS update to fuse into an operator's first (r2c) transform.
+struct CgFuse {
+  int mode = 0;                      // 1: model side (forward), 2: data side (adjoint)
+  const float* s = nullptr;          // s (mode 1) or q (mode 2)
+  float* u = nullptr;                // u (mode 1)
+  const float4* coef = nullptr;      // per gather (cs, beta, alpha, -)
 };
 
 // Arguments of the fused t-FFT + Stolt map + sum/spray row kernels.
@@ -142,6 +161,7 @@ struct ashrt_plan {
   float* qv = nullptr;       // data-sized
   float* wr = nullptr;       // data-sized
   float* y = nullptr;        // data-sized
+  float4* cg_coef = nullptr; // [2][max_batch] fused CGLS coefficients (forward, adjoint)
   double* scal = nullptr;    // per-gather scalars
   unsigned int* sel = nullptr;   // per-gather selection scratch
   int* flags = nullptr;      // per-gather status flags

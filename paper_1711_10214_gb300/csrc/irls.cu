@@ -377,6 +377,43 @@ __global__ void k_upd_p(float* __restrict__ p, const float* __restrict__ s, long
   if (mu > 0.f) block_add((double)mu * acc.value(), scal + (S_DEL0 + ((it + 1) & 1)) * B + g);
 }
 
+// Coefficients of the CGLS updates fused into the transforms (mu = 0 path).
+// Forward of iteration it: p_it = s_it + beta p_{it-1} (p_0 = s_0), and the
+// deferred u += alpha_{it-1} p_{it-1}; a stopped gather keeps p and u.
+__global__ void k_cg_coef_fwd(const double* scal, int B, int it, float4* coef) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B) return;
+  if (it == 0) {
+    coef[g] = make_float4(1.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const double gprev = scal[(S_GAM0 + ((it - 1) & 1)) * B + g];
+  const double gcur = scal[(S_GAM0 + (it & 1)) * B + g];
+  const bool act = scal[S_ACTIVE * B + g] != 0.0 && gprev > 0.0;
+  const float alpha = (float)cg_alpha(scal, B, g, it - 1);
+  coef[g] = act ? make_float4(1.f, (float)(gcur / gprev), alpha, 0.f)
+                : make_float4(0.f, 1.f, alpha, 0.f);
+}
+
+// Adjoint of iteration it: r -= alpha_it q_it.
+__global__ void k_cg_coef_adj(const double* scal, int B, int it, float4* coef) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B) return;
+  coef[g] = make_float4(0.f, 0.f, (float)cg_alpha(scal, B, g, it), 0.f);
+}
+
+// u += alpha_it p (the last CGLS iteration's model update)
+__global__ void k_upd_u(float* __restrict__ u, const float* __restrict__ p, long long nm,
+                        const double* scal, int B, int it) {
+  const int g = blockIdx.y;
+  const float a = (float)cg_alpha(scal, B, g, it);
+  if (a == 0.f) return;
+  const long long om = (long long)g * nm;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nm;
+       i += (long long)gridDim.x * blockDim.x)
+    u[om + i] = fmaf(a, p[om + i], u[om + i]);
+}
+
 // p = s at the start of CGLS; delta_0 = mu ||p||^2
 __global__ void k_copy_p(float* __restrict__ p, const float* __restrict__ s, long long nm,
                          double* scal, int B, float mu) {
@@ -592,22 +629,58 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
       CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm, o.mu > 0 ? nullptr : scal + S_GAM0 * B, B, s));
       ++applies_a;
       if (o.mu > 0) LAUNCH(k_smu, gm, kThreads, P->sv, P->u, nm, muf, scal + S_GAM0 * B, B);
-      LAUNCH(k_copy_p, gm, kThreads, P->pv, P->sv, nm, scal, B, muf);
-      for (int it = 0; it < o.n_cg; ++it) {
-        // delta_it (+= ||A p||^2; the mu ||p||^2 part was added when p was formed)
-        CK(op_forward(P, P->pv, P->qv, P->wminv, P->wr, tm, scal + (S_DEL0 + (it & 1)) * B, B, s));
-        ++applies_f;
-        LAUNCH(k_upd_ur, gm, kThreads, P->u, P->pv, nm, P->r, P->qv, nd, scal, B, it);
-        const int nxt = (it + 1) & 1;
-        CK(cudaMemsetAsync(scal + (S_GAM0 + nxt) * B, 0, sizeof(double) * B, s));
-        CK(cudaMemsetAsync(scal + (S_DEL0 + nxt) * B, 0, sizeof(double) * B, s));
-        CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm,
-                      o.mu > 0 ? nullptr : scal + (S_GAM0 + nxt) * B, B, s));
-        ++applies_a;
-        if (o.mu > 0)
+      // The adjoint after the last iteration's update would only serve a
+      // next direction: it is not run.
+      if (o.mu > 0) {
+        LAUNCH(k_copy_p, gm, kThreads, P->pv, P->sv, nm, scal, B, muf);
+        for (int it = 0; it < o.n_cg; ++it) {
+          // delta_it (+= ||A p||^2; the mu ||p||^2 part was added when p was formed)
+          CK(op_forward(P, P->pv, P->qv, P->wminv, P->wr, tm, scal + (S_DEL0 + (it & 1)) * B, B, s));
+          ++applies_f;
+          LAUNCH(k_upd_ur, gm, kThreads, P->u, P->pv, nm, P->r, P->qv, nd, scal, B, it);
+          if (it + 1 == o.n_cg) break;
+          const int nxt = (it + 1) & 1;
+          CK(cudaMemsetAsync(scal + (S_GAM0 + nxt) * B, 0, sizeof(double) * B, s));
+          CK(cudaMemsetAsync(scal + (S_DEL0 + nxt) * B, 0, sizeof(double) * B, s));
+          CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm, nullptr, B, s));
+          ++applies_a;
           LAUNCH(k_smu, gm, kThreads, P->sv, P->u, nm, muf, scal + (S_GAM0 + nxt) * B, B);
-        LAUNCH(k_upd_p, gm, kThreads, P->pv, P->sv, nm, scal, B, it, muf);
-        CK(cudaGetLastError());
+          LAUNCH(k_upd_p, gm, kThreads, P->pv, P->sv, nm, scal, B, it, muf);
+          CK(cudaGetLastError());
+        }
+      } else {
+        // mu = 0: the vector updates ride on the transforms' loads.  The
+        // forward of iteration it forms p_it = s_it + beta p_{it-1} and applies
+        // the deferred u += alpha_{it-1} p_{it-1}; the adjoint forms
+        // r -= alpha_it q_it.  The last iteration's u update runs on its own.
+        float4* cf_f = P->cg_coef;
+        float4* cf_a = P->cg_coef + B;
+        for (int it = 0; it < o.n_cg; ++it) {
+          LAUNCH(k_cg_coef_fwd, (B + 127) / 128, 128, scal, B, it, cf_f);
+          CgFuse ff;
+          ff.mode = 1;
+          ff.s = P->sv;
+          ff.u = P->u;
+          ff.coef = cf_f;
+          CK(op_forward(P, P->pv, P->qv, P->wminv, P->wr, tm, scal + (S_DEL0 + (it & 1)) * B, B,
+                        s, &ff));
+          ++applies_f;
+          if (it + 1 == o.n_cg) {
+            LAUNCH(k_upd_u, gm, kThreads, P->u, P->pv, nm, scal, B, it);
+            break;
+          }
+          LAUNCH(k_cg_coef_adj, (B + 127) / 128, 128, scal, B, it, cf_a);
+          const int nxt = (it + 1) & 1;
+          CK(cudaMemsetAsync(scal + (S_GAM0 + nxt) * B, 0, sizeof(double) * B, s));
+          CK(cudaMemsetAsync(scal + (S_DEL0 + nxt) * B, 0, sizeof(double) * B, s));
+          CgFuse fa;
+          fa.mode = 2;
+          fa.s = P->qv;
+          fa.coef = cf_a;
+          CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm, scal + (S_GAM0 + nxt) * B, B, s, &fa));
+          ++applies_a;
+          CK(cudaGetLastError());
+        }
       }
       // ---- m = W_m^-1 u, y = C L m (no mask), residual and misfit J_k
       LAUNCH(k_model, gm, kThreads, m, P->wminv, P->u, nm, scal, B);

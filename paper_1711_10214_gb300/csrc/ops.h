@@ -14,11 +14,13 @@ constexpr int kSelStride = 2048;
 size_t model_elems(const ashrt_plan* p);
 size_t data_elems(const ashrt_plan* p);
 
+// cg (optional): a CGLS update fused into the operator's first transform, on
+// the input m (forward, mode 1) or d (adjoint, mode 2), which is then written.
 cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const float* ew_model,
                        const float* ew_data, const float* tmask, double* dot, int batch,
-                       cudaStream_t s);
+                       cudaStream_t s, const CgFuse* cg = nullptr);
 cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const float* ew_model,
                        const float* ew_data, const float* tmask, double* dot, int batch,
-                       cudaStream_t s);
+                       cudaStream_t s, const CgFuse* cg = nullptr);
 
 }  // namespace ashrt

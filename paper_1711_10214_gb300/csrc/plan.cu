@@ -129,7 +129,7 @@ static ashrt_status cuda_fail(cudaError_t e, const char* what) {
 static void free_plan_memory(ashrt_plan* p) {
   void* ptrs[] = {p->tw_t, p->tw_x, p->wt, p->kmin, p->acone, p->taps, p->ks, p->phase, p->X, p->Y,
                   p->u, p->pv, p->sv, p->wminv, p->r, p->qv, p->wr, p->y,
-                  p->scal, p->sel, p->flags};
+                  p->scal, p->sel, p->flags, p->cg_coef};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -166,7 +166,7 @@ size_t data_elems(const ashrt_plan* p) { return (size_t)p->nx * p->nt; }
 //   adjoint: m = ew_model * L^T(tmask * ew_data * d); dot[g] += ||m_g||^2
 cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const float* ew_model,
                        const float* ew_data, const float* tmask, double* dot, int batch,
-                       cudaStream_t s) {
+                       cudaStream_t s, const CgFuse* cg) {
   XfftArgs ax;
   ax.in_real = m;
   ax.out_cplx = p->X;
@@ -182,6 +182,13 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
   ax.slabs = batch * p->P;
   ax.tw = p->tw_x;
   ax.cols = p->xfft_cols;
+  if (cg && cg->mode == 1) {
+    ax.cg_mode = 1;
+    ax.cg_io = const_cast<float*>(m);
+    ax.cg_s = cg->s;
+    ax.cg_u = cg->u;
+    ax.cg_coef = cg->coef;
+  }
   prof_begin(PROF_XR2C, s);
   cudaError_t e = launch_xfft_r2c(ax, s);
   prof_end(PROF_XR2C, s);
@@ -230,7 +237,7 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
 
 cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const float* ew_model,
                        const float* ew_data, const float* tmask, double* dot, int batch,
-                       cudaStream_t s) {
+                       cudaStream_t s, const CgFuse* cg) {
   XfftArgs ay;
   ay.in_real = d;
   ay.out_cplx = p->Y;
@@ -247,6 +254,12 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
   ay.slabs = batch;
   ay.tw = p->tw_x;
   ay.cols = p->xfft_cols;
+  if (cg && cg->mode == 2) {
+    ay.cg_mode = 2;
+    ay.cg_io = const_cast<float*>(d);
+    ay.cg_s = cg->s;
+    ay.cg_coef = cg->coef;
+  }
   prof_begin(PROF_XR2C, s);
   cudaError_t e = launch_xfft_r2c(ay, s);
   prof_end(PROF_XR2C, s);
@@ -478,6 +491,7 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
     chk(dev_alloc(&p->scal, B * kScalStride, &total));
     chk(dev_alloc(&p->sel, B * kSelStride, &total));
     chk(dev_alloc(&p->flags, 2 * B + 1, &total));
+    chk(dev_alloc(&p->cg_coef, 2 * B, &total));
   }
   if (st == ASHRT_OK) {
     // the padding columns of the spectra rows are never written: keep them zero

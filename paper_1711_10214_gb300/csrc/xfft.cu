@@ -89,6 +89,44 @@ __device__ __forceinline__ float2 load_pair_real(const float* __restrict__ row, 
   return make_float2(t < nt ? __ldg(row + t) : 0.f, t + 1 < nt ? __ldg(row + t + 1) : 0.f);
 }
 
+// Plain (coherent) pair load / store of samples t, t+1 of a row, for the
+// in-place CGLS updates (each pair is read and written by one thread).
+__device__ __forceinline__ float2 ld_pair(const float* row, int t, int nt, bool vec) {
+  if (vec && t + 1 < nt) return *(const float2*)(row + t);
+  return make_float2(t < nt ? row[t] : 0.f, t + 1 < nt ? row[t + 1] : 0.f);
+}
+
+__device__ __forceinline__ void st_pair(float* row, int t, int nt, bool vec, float2 v) {
+  if (vec && t + 1 < nt) {
+    *(float2*)(row + t) = v;
+    return;
+  }
+  if (t < nt) row[t] = v.x;
+  if (t + 1 < nt) row[t + 1] = v.y;
+}
+
+// The fused CGLS update of one sample pair (see XfftArgs::cg_mode); returns
+// the updated vector's pair, which is what the transform consumes.
+__device__ __forceinline__ float2 cg_update_pair(const XfftArgs& a, long long off, int t, bool vec,
+                                                 float4 cf) {
+  float* io = a.cg_io + off;
+  const float2 x = ld_pair(io, t, a.nt, vec);
+  const float2 y = ld_pair(a.cg_s + off, t, a.nt, vec);
+  float2 z;
+  if (a.cg_mode == 1) {
+    z = make_float2(fmaf(cf.x, y.x, cf.y * x.x), fmaf(cf.x, y.y, cf.y * x.y));
+    if (cf.z != 0.f) {
+      float* u = a.cg_u + off;
+      const float2 uo = ld_pair(u, t, a.nt, vec);
+      st_pair(u, t, a.nt, vec, make_float2(fmaf(cf.z, x.x, uo.x), fmaf(cf.z, x.y, uo.y)));
+    }
+  } else {
+    z = make_float2(fmaf(-cf.z, y.x, x.x), fmaf(-cf.z, y.y, x.y));
+  }
+  st_pair(io, t, a.nt, vec, z);
+  return z;
+}
+
 template <int LOGN, int C>
 __global__ void __launch_bounds__((1 << LOGN) * C / 16)
 xfft_r2c_kernel(XfftArgs a) {
@@ -103,6 +141,7 @@ xfft_r2c_kernel(XfftArgs a) {
   const float* in = a.in_real + slab * a.slab_real;
   const float* ew = a.ew ? a.ew + slab * a.slab_real : nullptr;
   const float* tm = a.tmask ? a.tmask + (slab / a.slabs_per_gather) * a.nx : nullptr;
+  const float4 cf = a.cg_mode ? a.cg_coef[slab / a.slabs_per_gather] : make_float4(0.f, 0.f, 0.f, 0.f);
 
   // first pass (radix 8, Ns = 1) for both butterflies of this thread: all
   // loads first; rows >= nx are the zero padding
@@ -116,7 +155,8 @@ xfft_r2c_kernel(XfftArgs a) {
       float2 z = make_float2(0.f, 0.f);
       if (row < a.nx) {
         const long long o = (long long)row * a.nt;
-        z = load_pair_real(in + o, ta, a.nt, vec);
+        z = a.cg_mode ? cg_update_pair(a, slab * a.slab_real + o, ta, vec, cf)
+                      : load_pair_real(in + o, ta, a.nt, vec);
         if (ew) {
           const float2 w = load_pair_real(ew + o, ta, a.nt, vec);
           z.x *= w.x;
