@@ -38,6 +38,8 @@ struct XfftArgs {
   const float* cg_s = nullptr;       // s (mode 1) or q (mode 2)
   float* cg_u = nullptr;             // u (mode 1)
   const float4* cg_coef = nullptr;   // [gathers]
+  int tma = 1;                       // r2c: use the persistent TMA kernel where it applies
+  int* err = nullptr;                // set to 1 if a bounded device wait ran out
 };
 
 // A CGLS update to fuse into an operator's first (r2c) transform.
@@ -162,6 +164,7 @@ struct ashrt_plan {
   float* wr = nullptr;       // data-sized
   float* y = nullptr;        // data-sized
   float4* cg_coef = nullptr; // [2][max_batch] fused CGLS coefficients (forward, adjoint)
+  int* dev_err = nullptr;    // set by a device wait that ran out (checked by the solver)
   double* scal = nullptr;    // per-gather scalars
   unsigned int* sel = nullptr;   // per-gather selection scratch
   int* flags = nullptr;      // per-gather status flags

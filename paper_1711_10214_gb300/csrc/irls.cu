@@ -759,7 +759,14 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
                      cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(fl.data(), flags, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(outer_cnt_h.data(), outer_cnt, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+  int dev_err = 0;
+  CK(cudaMemcpyAsync(&dev_err, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (dev_err) {
+    cudaMemsetAsync(P->dev_err, 0, sizeof(int), s);
+    set_error("robust_irls_deblend: a device-side wait for a tile copy ran out");
+    return ASHRT_ETIMEOUT;
+  }
 #undef CK
   if (rep) {
     for (int g = 0; g < B; ++g) {

@@ -129,7 +129,7 @@ static ashrt_status cuda_fail(cudaError_t e, const char* what) {
 static void free_plan_memory(ashrt_plan* p) {
   void* ptrs[] = {p->tw_t, p->tw_x, p->wt, p->kmin, p->acone, p->taps, p->ks, p->phase, p->X, p->Y,
                   p->u, p->pv, p->sv, p->wminv, p->r, p->qv, p->wr, p->y,
-                  p->scal, p->sel, p->flags, p->cg_coef};
+                  p->scal, p->sel, p->flags, p->cg_coef, p->dev_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -182,6 +182,7 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
   ax.slabs = batch * p->P;
   ax.tw = p->tw_x;
   ax.cols = p->xfft_cols;
+  ax.err = p->dev_err;
   if (cg && cg->mode == 1) {
     ax.cg_mode = 1;
     ax.cg_io = const_cast<float*>(m);
@@ -254,6 +255,7 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
   ay.slabs = batch;
   ay.tw = p->tw_x;
   ay.cols = p->xfft_cols;
+  ay.err = p->dev_err;
   if (cg && cg->mode == 2) {
     ay.cg_mode = 2;
     ay.cg_io = const_cast<float*>(d);
@@ -478,6 +480,8 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
   const size_t xpan = (size_t)Lh * p->ld;
   if (st == ASHRT_OK) chk(dev_alloc(&p->X, B * p->P * xpan, &total));
   if (st == ASHRT_OK) chk(dev_alloc(&p->Y, B * xpan, &total));
+  if (st == ASHRT_OK) chk(dev_alloc(&p->dev_err, 1, &total));
+  if (st == ASHRT_OK && cudaMemset(p->dev_err, 0, sizeof(int)) != cudaSuccess) st = ASHRT_ECUDA;
   if (st == ASHRT_OK && p->with_solver) {
     const size_t me = B * model_elems(p), de = B * data_elems(p);
     chk(dev_alloc(&p->u, me, &total));

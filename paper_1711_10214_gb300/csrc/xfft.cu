@@ -18,8 +18,12 @@
 // what it stores (the CGLS norms) per gather.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "common.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace ashrt {
 
@@ -201,6 +205,157 @@ xfft_r2c_kernel(XfftArgs a) {
   }
 }
 
+// Persistent TMA variant of the r2c transform: 16 real time columns (C = 8
+// packed pairs) per tile, one CTA loops over tiles.  The input tile of every
+// vector the load needs (the transformed vector, and for the fused CGLS
+// update s / q and u, and the weight) is brought into shared memory by TMA
+// box loads [nx][16] that signal one mbarrier; as soon as the first pass has
+// consumed the staged tile (and the fused update has been written back by
+// TMA stores), the next tile's loads are issued, so they overlap the
+// remaining FFT passes and the spectrum stores of the current tile.
+// Requires nx <= 256 (one box per vector), nt % 4 == 0 and 16-byte aligned
+// vectors; the launcher falls back to xfft_r2c_kernel otherwise.
+struct R2cMaps {
+  CUtensorMap in, s, u, w;
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 2)
+xfft_r2c_tma(XfftArgs a, const __grid_constant__ R2cMaps mp, int n_tt, long long n_tiles) {
+  constexpr int N = 1 << LOGN, C = 8, T = N * C / 16, JS = T / C;
+  using S = Sched<LOGN>;
+  extern __shared__ unsigned char smraw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 127) & ~(uintptr_t)127);
+  const int mode = a.cg_mode;
+  const bool has_w = a.ew != nullptr;
+  const int box = a.nx * 16;                          // floats of one vector's box
+  const int slot = (box * 4 + 127) & ~127;            // bytes, 128-byte aligned
+  const int i_s = 1, i_u = mode ? 2 : 1, i_w = mode == 1 ? 3 : (mode ? 2 : 1);
+  const int nslot = 1 + (mode ? 1 : 0) + (mode == 1 ? 1 : 0) + (has_w ? 1 : 0);
+  float* st_in = (float*)base;
+  float* st_s = (float*)(base + i_s * slot);
+  float* st_u = (float*)(base + i_u * slot);
+  float* st_w = (float*)(base + i_w * slot);
+  float2* sm = (float2*)(base + nslot * slot);        // [N][C]
+  uint64_t* bar = (uint64_t*)(sm + N * C);
+  const int tid = threadIdx.x, col = tid % C, j0 = tid / C;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](long long tile) {
+    const int z = (int)(tile / n_tt), x = (int)(tile % n_tt) * 16;
+    mbar_arrive_expect_tx(bar, (uint32_t)(nslot * box * 4));
+    tma_load_3d(st_in, &mp.in, x, 0, z, bar);
+    if (mode) tma_load_3d(st_s, &mp.s, x, 0, z, bar);
+    if (mode == 1) tma_load_3d(st_u, &mp.u, x, 0, z, bar);
+    if (has_w) tma_load_3d(st_w, &mp.w, x, 0, z, bar);
+  };
+  long long tile = blockIdx.x;
+  if (tile < n_tiles && tid == 0) issue(tile);
+  uint32_t parity = 0;
+  for (; tile < n_tiles; tile += gridDim.x) {
+    const long long slab = tile / n_tt;
+    const int t0 = (int)(tile % n_tt) * 16;
+    const long long g = slab / a.slabs_per_gather;
+    const float* tm = a.tmask ? a.tmask + g * a.nx : nullptr;
+    const float4 cf = mode ? a.cg_coef[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool ok = mbar_wait_bounded(bar, parity);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        if (a.err) atomicExch(a.err, 1);
+        bulk_wait_all();
+      }
+      return;
+    }
+    parity ^= 1u;
+
+    // first pass from the staged tile (fused update written back in place)
+    float2 v[2][8];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int jb = j0 + JS * q;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int row = jb + r * (N / 8);
+        float2 z = make_float2(0.f, 0.f);
+        if (row < a.nx) {
+          const int e = row * 16 + 2 * col;
+          float2 x = *(const float2*)(st_in + e);
+          if (mode == 1) {
+            const float2 sv = *(const float2*)(st_s + e);
+            if (cf.z != 0.f) {
+              const float2 uo = *(const float2*)(st_u + e);
+              *(float2*)(st_u + e) = make_float2(fmaf(cf.z, x.x, uo.x), fmaf(cf.z, x.y, uo.y));
+            }
+            x = make_float2(fmaf(cf.x, sv.x, cf.y * x.x), fmaf(cf.x, sv.y, cf.y * x.y));
+            *(float2*)(st_in + e) = x;
+          } else if (mode == 2) {
+            const float2 qv = *(const float2*)(st_s + e);
+            x = make_float2(fmaf(-cf.z, qv.x, x.x), fmaf(-cf.z, qv.y, x.y));
+            *(float2*)(st_in + e) = x;
+          }
+          if (has_w) {
+            const float2 w = *(const float2*)(st_w + e);
+            x.x *= w.x;
+            x.y *= w.y;
+          }
+          if (tm) {
+            const float gm = __ldg(tm + row);
+            x.x *= gm;
+            x.y *= gm;
+          }
+          z = x;
+        }
+        v[q][r] = z;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int jb = j0 + JS * q;
+      dft8<-1>(v[q]);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) sm[(jb * 8 + r) * C + col] = v[q][r];
+    }
+    if (mode) fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      if (mode) {
+        tma_store_3d(&mp.in, t0, 0, (int)slab, st_in);
+        if (mode == 1 && cf.z != 0.f) tma_store_3d(&mp.u, t0, 0, (int)slab, st_u);
+        bulk_commit();
+        bulk_wait_read();
+      }
+      const long long nxt = tile + gridDim.x;
+      if (nxt < n_tiles) {
+        fence_proxy_async();
+        issue(nxt);
+      }
+    }
+    col_pass_range<-1, LOGN, C, 1, S::NPASS>(sm, a.tw, tid);
+
+    float2* out = a.out_cplx + slab * a.slab_cplx;
+    for (int f = tid; f < (N / 2 + 1) * C; f += T) {
+      const int l = f / C, c = f % C;
+      const float2 zl = sm[l * C + c];
+      const float2 zm = sm[((N - l) & (N - 1)) * C + c];
+      const float4 AB = make_float4(0.5f * (zl.x + zm.x), 0.5f * (zl.y - zm.y),
+                                    0.5f * (zl.y + zm.y), -0.5f * (zl.x - zm.x));
+      const int t = t0 + 2 * c;
+      float2* o = out + (long long)l * a.ld + t;
+      if (t + 1 < a.nt) {
+        *(float4*)o = AB;
+      } else if (t < a.nt) {
+        o[0] = make_float2(AB.x, AB.y);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) bulk_wait_all();
+}
+
 // Hermitian extension of a stored half spectrum for two adjacent columns at
 // once: row l of the full length-N spectrum; rows 0 and N/2 keep their real
 // parts only (real signal).  Returns (A, B) of columns t and t+1 (t even).
@@ -315,6 +470,44 @@ cudaError_t launch_r2c_v(const XfftArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int LOGN>
+cudaError_t launch_r2c_tma(const XfftArgs& a, cudaStream_t s, bool* used) {
+  constexpr int N = 1 << LOGN, C = 8, T = N * C / 16;
+  *used = false;
+  const long long slabs = a.slabs;
+  R2cMaps mp;
+  memset(&mp, 0, sizeof(mp));
+  const int mode = a.cg_mode;
+  if (!encode_tmap_f32_3d(&mp.in, a.in_real, a.nt, a.nx, slabs, 16, a.nx)) return cudaSuccess;
+  if (mode && !encode_tmap_f32_3d(&mp.s, a.cg_s, a.nt, a.nx, slabs, 16, a.nx)) return cudaSuccess;
+  if (mode == 1 && !encode_tmap_f32_3d(&mp.u, a.cg_u, a.nt, a.nx, slabs, 16, a.nx))
+    return cudaSuccess;
+  if (a.ew && !encode_tmap_f32_3d(&mp.w, a.ew, a.nt, a.nx, slabs, 16, a.nx)) return cudaSuccess;
+  const int nslot = 1 + (mode ? 1 : 0) + (mode == 1 ? 1 : 0) + (a.ew ? 1 : 0);
+  const size_t slot = ((size_t)a.nx * 64 + 127) & ~(size_t)127;
+  const size_t smem = 128 + nslot * slot + (size_t)N * C * sizeof(float2) + 16;
+  static int max_smem_set = 0;
+  if ((int)smem > max_smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(xfft_r2c_tma<LOGN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    max_smem_set = (int)smem;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xfft_r2c_tma<LOGN>, T, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n_tt = (a.nt + 15) / 16;
+  const long long n_tiles = slabs * n_tt;
+  const long long grid = std::min<long long>(n_tiles, (long long)sms * per_sm);
+  xfft_r2c_tma<LOGN><<<(unsigned)grid, T, smem, s>>>(a, mp, n_tt, n_tiles);
+  *used = true;
+  return cudaGetLastError();
+}
+
 template <int LOGN, int C>
 cudaError_t launch_c2r_v(const XfftArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN, T = N * C / 16;
@@ -358,6 +551,19 @@ int xfft_log2(int n) {
 }
 
 cudaError_t launch_xfft_r2c(const XfftArgs& a, cudaStream_t s) {
+  // the TMA kernel pays where the load streams several vectors (weights,
+  // fused CGLS update); a plain transform keeps the wider non-TMA tile
+  if (a.tma && (a.cg_mode || a.ew) && a.nx <= 256 && (a.nt & 3) == 0) {
+    bool used = false;
+    cudaError_t e = cudaSuccess;
+    switch (xfft_log2(a.Nx)) {
+      case 7: e = launch_r2c_tma<7>(a, s, &used); break;
+      case 8: e = launch_r2c_tma<8>(a, s, &used); break;
+      case 9: e = launch_r2c_tma<9>(a, s, &used); break;
+      default: break;
+    }
+    if (e != cudaSuccess || used) return e;
+  }
   switch (xfft_log2(a.Nx)) {
     case 4: return launch_r2c_t<4>(a, s);
     case 5: return launch_r2c_t<5>(a, s);
