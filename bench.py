@@ -43,14 +43,16 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="deblend", choices=["deblend", "ops"],
                     help="ops: time forward+adjoint operator pairs only (profiling aid)")
-    ap.add_argument("--batch", type=int, default=B, help="gathers per call in --mode ops")
+    ap.add_argument("--batch", type=int, default=B,
+                    help="gathers per call (the deblend workload is 64; smaller batches are "
+                         "for profiling captures)")
     return ap.parse_args()
 
 
-def _config(extra=None):
-    c = {"workload": "robust IRLS deblend, 64 gathers x (nt 1024 @ 4 ms, nx 256 @ 12.5 m), "
-                     "32 velocities x 256 apexes, IRLS 8 x 30, p = q = 1, 25 Hz wavelet",
-         "gathers_per_step": B, "nt": NT, "nx": NX, "nv": NV, "irls": [N_OUTER, N_CG],
+def _config(extra=None, batch=B):
+    c = {"workload": "robust IRLS deblend, %d gathers x (nt 1024 @ 4 ms, nx 256 @ 12.5 m), "
+                     "32 velocities x 256 apexes, IRLS 8 x 30, p = q = 1, 25 Hz wavelet" % batch,
+         "gathers_per_step": batch, "nt": NT, "nx": NX, "nv": NV, "irls": [N_OUTER, N_CG],
          "padded": [2048, 512], "l2": "inputs larger than L2 (model 2.1 GB per vector)",
          "parallelism": "replicas (gathers are independent; no collective)"}
     if extra:
@@ -201,6 +203,7 @@ def run_ours(args):
             dist.barrier()
 
     dev = torch.device("cuda", local)
+    B = args.batch
     c = synth.config2(B, NT, NX, NV)
     d_host = torch.from_numpy(c["blended"].astype(np.float32)).pin_memory()
     drec_host = torch.empty_like(d_host).pin_memory()
@@ -276,14 +279,14 @@ def run_ours(args):
     achieved = flops / per_launch_s / 1e12
     # DRAM bytes per launch of the dominant kernel, from one ncu capture of the
     # 8-gather launch of the same kernel (dram__bytes_read.sum +
-    # dram__bytes_write.sum = 580.0 MB), scaled by the gathers per launch
-    traffic = {"stolt_adj_rows": 580.0e6 / 8}.get(dom)
+    # dram__bytes_write.sum = 633.8 MB), scaled by the gathers per launch
+    traffic = {"stolt_adj_rows": 633.8e6 / 8}.get(dom)
     traffic = traffic * B if traffic is not None else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config(),
+        "config": _config(batch=B),
         "gathers_per_s": world * B * args.steps / t,
         "hbm_fraction_pair": {"algorithmic_bytes_per_pair": alg["pair_bytes"],
                               "achieved_gbs": value / world * alg["pair_bytes"] / 1e9,
