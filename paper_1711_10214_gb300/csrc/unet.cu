@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -332,8 +333,9 @@ __global__ void k_adam(float* w, const float* g, float* m, float* v, long long n
   }
 }
 
-// FP32 OIHW master -> BF16 [tap][ci][co] (forward) and flipped [tap'][co][ci] (input gradient)
-__global__ void k_wconv(const float* w, bf16* wf, bf16* wt, int co_n, int ci_n, int K) {
+// FP32 OIHW master -> BF16 [tap][ci][co] (forward, CUDA cores), flipped
+// [tap'][co][ci] (input gradient) and [tap][co][ci] (forward, tensor cores)
+__global__ void k_wconv(const float* w, bf16* wf, bf16* wt, bf16* wn, int co_n, int ci_n, int K) {
   const int total = co_n * ci_n * K * K;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int kx = i % K, ky = (i / K) % K, ci = (i / (K * K)) % ci_n, co = i / (K * K * ci_n);
@@ -341,6 +343,122 @@ __global__ void k_wconv(const float* w, bf16* wf, bf16* wt, int co_n, int ci_n, 
     const bf16 b = __float2bfloat16(w[i]);
     wf[((long long)tap * ci_n + ci) * co_n + co] = b;
     wt[((long long)tapf * co_n + co) * ci_n + ci] = b;
+    wn[((long long)tap * co_n + co) * ci_n + ci] = b;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core forward convolution (mma.sync m16n8k16, BF16 operands, FP32
+// accumulation) for layers whose input channels are a multiple of 16: an
+// implicit GEMM with M = pixels, N = output channels, K = taps x input
+// channels.  CTA: 128 consecutive pixels of one image row x NB*16 output
+// channels, 8 warps of 16 pixels each.  Per chunk of KC input channels the
+// three input rows (130 pixels with the halo) and the weights of all taps are
+// staged in shared memory (rows padded by 8 elements against bank conflicts)
+// and consumed by ldmatrix fragments; bias, ReLU and the BF16 (or FP32)
+// store are fused into the epilogue.
+__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
+                                        const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+struct MmaConvArgs {
+  Tensor in;             // bf16 NHWC slice, ps and off multiples of 8
+  const bf16* w;         // [K*K][Cout][Cin]
+  const float* bias;     // [Cout]
+  Tensor out;            // bf16 or fp32 NHWC slice
+  int N, H, W, Cin, Cout, relu;
+};
+
+template <int K, int KC, int NB, typename TO>
+__global__ void __launch_bounds__(256, 2) k_conv_mma(MmaConvArgs a) {
+  constexpr int R = K / 2, PW = 128 + 2 * R, LDA = KC + 8, NT = NB * 16, TAPS = K * K;
+  extern __shared__ __align__(16) unsigned char smc[];
+  bf16* xs = (bf16*)smc;                              // [K rows][PW px][LDA]
+  bf16* ws = xs + K * PW * LDA;                       // [TAPS][NT co][LDA]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int xt = (a.W + 127) / 128;
+  const int row = blockIdx.x / xt;
+  const int x0 = (blockIdx.x % xt) * 128;
+  const int n = row / a.H, y = row % a.H;
+  const int co0 = blockIdx.y * NT;
+  const bf16* in = (const bf16*)a.in.p;
+  float acc[2 * NB][4];
+#pragma unroll
+  for (int j = 0; j < 2 * NB; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+
+  for (int ci0 = 0; ci0 < a.Cin; ci0 += KC) {
+    // stage the input rows: 16-byte vectors of 8 channels
+    constexpr int VPX = KC / 8;
+    for (int e = tid; e < K * PW * VPX; e += 256) {
+      const int v = e % VPX, px = (e / VPX) % PW, r = e / (VPX * PW);
+      const int yy = y + r - R, xx = x0 + px - R;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+        val = *(const uint4*)(in + (((long long)n * a.H + yy) * a.W + xx) * a.in.ps + a.in.off +
+                              ci0 + 8 * v);
+      *(uint4*)(xs + (r * PW + px) * LDA + 8 * v) = val;
+    }
+    for (int e = tid; e < TAPS * NT * VPX; e += 256) {
+      const int v = e % VPX, c = (e / VPX) % NT, tap = e / (VPX * NT);
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (co0 + c < a.Cout)
+        val = *(const uint4*)(a.w + ((long long)tap * a.Cout + co0 + c) * a.Cin + ci0 + 8 * v);
+      *(uint4*)(ws + (tap * NT + c) * LDA + 8 * v) = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int tap = 0; tap < TAPS; ++tap) {
+      const int dy = tap / K, dx = tap % K;
+#pragma unroll
+      for (int kk = 0; kk < KC; kk += 16) {
+        uint32_t a0, a1, a2, a3;
+        // A: rows = the warp's 16 pixels (shifted by dx), k = channels kk..kk+15
+        const int ar = lane & 15, ak = kk + ((lane >> 4) << 3);
+        ldsm_x4(a0, a1, a2, a3, xs + (dy * PW + warp * 16 + ar + dx) * LDA + ak);
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb) {
+          // B: two n8 blocks of 16 output channels, k = channels kk..kk+15
+          uint32_t b0, b1, b2, b3;
+          const int bn = nb * 16 + (lane & 7) + ((lane >> 4) << 3), bk = kk + (((lane >> 3) & 1) << 3);
+          ldsm_x4(b0, b1, b2, b3, ws + (tap * NT + bn) * LDA + bk);
+          mma_bf16(acc[2 * nb], a0, a1, a2, a3, b0, b1);
+          mma_bf16(acc[2 * nb + 1], a0, a1, a2, a3, b2, b3);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // epilogue: c0, c1 at (pixel g, channels 2t, 2t+1), c2, c3 at pixel g + 8
+  const int g = lane >> 2, t = lane & 3;
+  TO* out = (TO*)a.out.p;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int xx = x0 + warp * 16 + g + 8 * h;
+    if (xx >= a.W) continue;
+    const long long pix = ((long long)n * a.H + y) * a.W + xx;
+#pragma unroll
+    for (int j = 0; j < 2 * NB; ++j) {
+      const int co = co0 + 8 * j + 2 * t;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (co + u >= a.Cout) continue;
+        float v = acc[j][2 * h + u] + a.bias[co + u];
+        if (a.relu) v = fmaxf(v, 0.f);
+        st_f(out, pix * a.out.ps + a.out.off + co + u, v);
+      }
+    }
   }
 }
 
@@ -393,7 +511,7 @@ __global__ void k_predict_out(const float* y, const float* rms, float* m0, float
 struct Layer {
   int ci, co, k;
   long long w_off, b_off;   // into the flat parameter buffer
-  bf16 *wf = nullptr, *wt = nullptr;
+  bf16 *wf = nullptr, *wt = nullptr, *wn = nullptr;
 };
 
 int grid1d(long long n) {
@@ -460,6 +578,58 @@ void conv(Tensor in, Tensor mask, const bf16* w, const float* bias, Tensor out, 
   count_launches(1);
 }
 
+template <int K, int KC, int NB, typename TO>
+void conv_mma_v(const MmaConvArgs& a, cudaStream_t s) {
+  constexpr int R = K / 2, PW = 128 + 2 * R, LDA = KC + 8;
+  const size_t smem = (size_t)(K * PW * LDA + K * K * NB * 16 * LDA) * sizeof(bf16);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv_mma<K, KC, NB, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
+  dim3 grid((unsigned)((long long)a.N * a.H * ((a.W + 127) / 128)), (a.Cout + NB * 16 - 1) / (NB * 16));
+  k_conv_mma<K, KC, NB, TO><<<grid, 256, smem, s>>>(a);
+  count_launches(1);
+}
+
+// Tensor-core forward convolution (input channels a multiple of 16, channel
+// strides and offsets multiples of 8): picks the channel chunk and the
+// output-channel tile from the layer's sizes.
+template <int K, typename TO>
+void conv_mma(Tensor in, const bf16* w, const float* bias, Tensor out, int N, int H, int W,
+              int Cin, int Cout, int relu, cudaStream_t s) {
+  MmaConvArgs a;
+  a.in = in;
+  a.w = w;
+  a.bias = bias;
+  a.out = out;
+  a.N = N;
+  a.H = H;
+  a.W = W;
+  a.Cin = Cin;
+  a.Cout = Cout;
+  a.relu = relu;
+  const bool kc32 = Cin % 32 == 0;
+  const int nb = Cout % 64 == 0 ? 4 : Cout % 48 == 0 ? 3 : Cout % 32 == 0 ? 2 : Cout <= 16 ? 1
+               : std::min(4, (Cout + 15) / 16);
+  if (kc32) {
+    switch (nb) {
+      case 1: conv_mma_v<K, 32, 1, TO>(a, s); break;
+      case 2: conv_mma_v<K, 32, 2, TO>(a, s); break;
+      case 3: conv_mma_v<K, 32, 3, TO>(a, s); break;
+      default: conv_mma_v<K, 32, 4, TO>(a, s); break;
+    }
+  } else {
+    switch (nb) {
+      case 1: conv_mma_v<K, 16, 1, TO>(a, s); break;
+      case 2: conv_mma_v<K, 16, 2, TO>(a, s); break;
+      case 3: conv_mma_v<K, 16, 3, TO>(a, s); break;
+      default: conv_mma_v<K, 16, 4, TO>(a, s); break;
+    }
+  }
+}
+
 template <int K>
 void wgrad(Tensor in, Tensor g, Tensor mask, float* gw, float* gb, int N, int H, int W, int Cin,
            int Cout, cudaStream_t s) {
@@ -497,27 +667,27 @@ void net_forward(ashrt_unet* u, int n, cudaStream_t s) {
   auto grid = [&](long long cnt) { return grid1d(cnt); };
   // encoder
   conv<3, bf16, bf16>(T_(u->x, 1), none, L[0].wf, B(0), T_(u->e1a, c0), n, H, W, 1, c0, 1, s);
-  conv<3, bf16, bf16>(T_(u->e1a, c0), none, L[1].wf, B(1), T_(u->cat1, c1 + c0, c1), n, H, W, c0, c0, 1, s);
+  conv_mma<3, bf16>(T_(u->e1a, c0), L[1].wn, B(1), T_(u->cat1, c1 + c0, c1), n, H, W, c0, c0, 1, s);
   k_pool<<<grid((long long)n * H * W / 4 * c0), 256, 0, s>>>(T_(u->cat1, c1 + c0, c1), T_(u->p1, c0), n, H, W, c0);
-  conv<3, bf16, bf16>(T_(u->p1, c0), none, L[2].wf, B(2), T_(u->e2a, c1), n, H / 2, W / 2, c0, c1, 1, s);
-  conv<3, bf16, bf16>(T_(u->e2a, c1), none, L[3].wf, B(3), T_(u->cat2, c2 + c1, c2), n, H / 2, W / 2, c1, c1, 1, s);
+  conv_mma<3, bf16>(T_(u->p1, c0), L[2].wn, B(2), T_(u->e2a, c1), n, H / 2, W / 2, c0, c1, 1, s);
+  conv_mma<3, bf16>(T_(u->e2a, c1), L[3].wn, B(3), T_(u->cat2, c2 + c1, c2), n, H / 2, W / 2, c1, c1, 1, s);
   k_pool<<<grid((long long)n * H * W / 16 * c1), 256, 0, s>>>(T_(u->cat2, c2 + c1, c2), T_(u->p2, c1), n, H / 2, W / 2, c1);
-  conv<3, bf16, bf16>(T_(u->p2, c1), none, L[4].wf, B(4), T_(u->e3a, c2), n, H / 4, W / 4, c1, c2, 1, s);
-  conv<3, bf16, bf16>(T_(u->e3a, c2), none, L[5].wf, B(5), T_(u->cat3, c3 + c2, c3), n, H / 4, W / 4, c2, c2, 1, s);
+  conv_mma<3, bf16>(T_(u->p2, c1), L[4].wn, B(4), T_(u->e3a, c2), n, H / 4, W / 4, c1, c2, 1, s);
+  conv_mma<3, bf16>(T_(u->e3a, c2), L[5].wn, B(5), T_(u->cat3, c3 + c2, c3), n, H / 4, W / 4, c2, c2, 1, s);
   k_pool<<<grid((long long)n * H * W / 64 * c2), 256, 0, s>>>(T_(u->cat3, c3 + c2, c3), T_(u->p3, c2), n, H / 4, W / 4, c2);
-  conv<3, bf16, bf16>(T_(u->p3, c2), none, L[6].wf, B(6), T_(u->ba, c3), n, H / 8, W / 8, c2, c3, 1, s);
-  conv<3, bf16, bf16>(T_(u->ba, c3), none, L[7].wf, B(7), T_(u->bb, c3), n, H / 8, W / 8, c3, c3, 1, s);
+  conv_mma<3, bf16>(T_(u->p3, c2), L[6].wn, B(6), T_(u->ba, c3), n, H / 8, W / 8, c2, c3, 1, s);
+  conv_mma<3, bf16>(T_(u->ba, c3), L[7].wn, B(7), T_(u->bb, c3), n, H / 8, W / 8, c3, c3, 1, s);
   // decoder
   k_up<<<grid((long long)n * H * W / 16 * c3), 256, 0, s>>>(T_(u->bb, c3), T_(u->cat3, c3 + c2, 0), n, H / 4, W / 4, c3);
-  conv<3, bf16, bf16>(T_(u->cat3, c3 + c2), none, L[8].wf, B(8), T_(u->d3a, c2), n, H / 4, W / 4, c3 + c2, c2, 1, s);
-  conv<3, bf16, bf16>(T_(u->d3a, c2), none, L[9].wf, B(9), T_(u->d3b, c2), n, H / 4, W / 4, c2, c2, 1, s);
+  conv_mma<3, bf16>(T_(u->cat3, c3 + c2), L[8].wn, B(8), T_(u->d3a, c2), n, H / 4, W / 4, c3 + c2, c2, 1, s);
+  conv_mma<3, bf16>(T_(u->d3a, c2), L[9].wn, B(9), T_(u->d3b, c2), n, H / 4, W / 4, c2, c2, 1, s);
   k_up<<<grid((long long)n * H * W / 4 * c2), 256, 0, s>>>(T_(u->d3b, c2), T_(u->cat2, c2 + c1, 0), n, H / 2, W / 2, c2);
-  conv<3, bf16, bf16>(T_(u->cat2, c2 + c1), none, L[10].wf, B(10), T_(u->d2a, c1), n, H / 2, W / 2, c2 + c1, c1, 1, s);
-  conv<3, bf16, bf16>(T_(u->d2a, c1), none, L[11].wf, B(11), T_(u->d2b, c1), n, H / 2, W / 2, c1, c1, 1, s);
+  conv_mma<3, bf16>(T_(u->cat2, c2 + c1), L[10].wn, B(10), T_(u->d2a, c1), n, H / 2, W / 2, c2 + c1, c1, 1, s);
+  conv_mma<3, bf16>(T_(u->d2a, c1), L[11].wn, B(11), T_(u->d2b, c1), n, H / 2, W / 2, c1, c1, 1, s);
   k_up<<<grid((long long)n * H * W * c1), 256, 0, s>>>(T_(u->d2b, c1), T_(u->cat1, c1 + c0, 0), n, H, W, c1);
-  conv<3, bf16, bf16>(T_(u->cat1, c1 + c0), none, L[12].wf, B(12), T_(u->d1a, c0), n, H, W, c1 + c0, c0, 1, s);
-  conv<3, bf16, bf16>(T_(u->d1a, c0), none, L[13].wf, B(13), T_(u->d1b, c0), n, H, W, c0, c0, 1, s);
-  conv<1, bf16, float>(T_(u->d1b, c0), none, L[14].wf, B(14), T_(u->y, u->cout), n, H, W, c0, u->cout, 0, s);
+  conv_mma<3, bf16>(T_(u->cat1, c1 + c0), L[12].wn, B(12), T_(u->d1a, c0), n, H, W, c1 + c0, c0, 1, s);
+  conv_mma<3, bf16>(T_(u->d1a, c0), L[13].wn, B(13), T_(u->d1b, c0), n, H, W, c0, c0, 1, s);
+  conv_mma<1, float>(T_(u->d1b, c0), L[14].wn, B(14), T_(u->y, u->cout), n, H, W, c0, u->cout, 0, s);
   count_launches(6);
 }
 
@@ -582,7 +752,7 @@ void net_backward(ashrt_unet* u, int n, cudaStream_t s) {
 cudaError_t refresh_bf16_weights(ashrt_unet* u, cudaStream_t s) {
   for (auto& l : u->L) {
     const int total = l.co * l.ci * l.k * l.k;
-    k_wconv<<<(total + 255) / 256, 256, 0, s>>>(u->w + l.w_off, l.wf, l.wt, l.co, l.ci, l.k);
+    k_wconv<<<(total + 255) / 256, 256, 0, s>>>(u->w + l.w_off, l.wf, l.wt, l.wn, l.co, l.ci, l.k);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -634,6 +804,7 @@ ashrt_status ashrt_unet_create(ashrt_unet** out, int H, int W, int out_channels,
   for (auto& l : u->L) {
     A(&l.wf, (size_t)l.co * l.ci * l.k * l.k);
     A(&l.wt, (size_t)l.co * l.ci * l.k * l.k);
+    A(&l.wn, (size_t)l.co * l.ci * l.k * l.k);
   }
   A(&u->x, P0);
   A(&u->e1a, P0 * c0);
