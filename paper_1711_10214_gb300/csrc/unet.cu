@@ -233,16 +233,22 @@ __global__ void k_pool_bwd_acc(Tensor gout, Tensor gin, int N, int H, int W, int
   }
 }
 
-// nearest 2x upsampling (forward, bf16) and its transpose (fp32, written)
+// nearest 2x upsampling (forward, bf16; 8 channels = 16 bytes per thread, C,
+// strides and offsets multiples of 8) and its transpose (fp32, written)
 __global__ void k_up(Tensor in, Tensor out, int N, int H, int W, int C) {   // H, W: output sizes
-  const long long total = (long long)N * H * W * C;
+  const int C8 = C / 8;
+  const long long total = (long long)N * H * W * C8;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    const long long p = i / C;
-    const int x = (int)(p % W), y = (int)((p / W) % H), n = (int)(p / ((long long)W * H));
-    const long long q = ((long long)n * (H / 2) + y / 2) * (W / 2) + x / 2;
-    ((bf16*)out.p)[p * out.ps + out.off + c] = ((const bf16*)in.p)[q * in.ps + in.off + c];
+    const int c = (int)(i % C8) * 8;
+    const long long p = i / C8;
+    const int x = (int)(p % W);
+    const long long ny = p / W;                 // n * H + y
+    const int y = (int)(ny % H);
+    const long long n = ny / H;
+    const long long q = (n * (H / 2) + y / 2) * (W / 2) + x / 2;
+    *(uint4*)((bf16*)out.p + p * out.ps + out.off + c) =
+        *(const uint4*)((const bf16*)in.p + q * in.ps + in.off + c);
   }
 }
 
@@ -270,10 +276,16 @@ __global__ void k_pack_in(const float* d, const float* rms, bf16* x, long long p
     x[i] = __float2bfloat16(d[i] / rms[i / per]);
 }
 
-__global__ void k_rms(const float* d, long long per, float* rms) {
-  const int n = blockIdx.x;
+// sum of squares of every gather, many CTAs per gather (FP64 partials, one
+// atomic per CTA), then rms = sqrt(sum / per)
+__global__ void k_sumsq(const float* d, long long per, double* acc) {
+  const int n = blockIdx.y;
   double s = 0.0;
-  for (long long i = threadIdx.x; i < per; i += blockDim.x) s += (double)d[n * per + i] * d[n * per + i];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = d[n * per + i];
+    s += v * v;
+  }
   __shared__ double red[256];
   red[threadIdx.x] = s;
   __syncthreads();
@@ -281,17 +293,59 @@ __global__ void k_rms(const float* d, long long per, float* rms) {
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) rms[n] = (float)fmax(sqrt(red[0] / (double)per), 1e-30);
+  if (threadIdx.x == 0) atomicAdd(acc + n, red[0]);
 }
 
-// NHWC head output [N][P][cout] -> planar [N][cout][P] (P = pixels)
+__global__ void k_rms_fin(const double* acc, long long per, float* rms, int N) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) rms[n] = (float)fmax(sqrt(acc[n] / (double)per), 1e-30);
+}
+
+// First layer (one input channel -> 16): one thread per pixel, the 3x3
+// neighbourhood from the BF16 image, weights [9][16] from shared memory,
+// 16 BF16 outputs written as two 16-byte vectors (out.ps, out.off multiples of 8).
+__global__ void k_conv_first(const bf16* x, const bf16* w, const float* bias, Tensor out, int N,
+                             int H, int W, int relu) {
+  __shared__ float ws[9][16];
+  __shared__ float bs[16];
+  if (threadIdx.x < 144) ws[threadIdx.x / 16][threadIdx.x % 16] = __bfloat162float(w[threadIdx.x]);
+  if (threadIdx.x < 16) bs[threadIdx.x] = bias[threadIdx.x];
+  __syncthreads();
+  const long long total = (long long)N * H * W;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int xx = (int)(p % W);
+    const long long ny = p / W;
+    const int y = (int)(ny % H);
+    const long long n = ny / H;
+    float acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = bs[c];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int yy = y + t / 3 - 1, xc = xx + t % 3 - 1;
+      const float v = (yy >= 0 && yy < H && xc >= 0 && xc < W)
+                          ? __bfloat162float(x[(n * H + yy) * W + xc]) : 0.f;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[c] = fmaf(v, ws[t][c], acc[c]);
+    }
+    __align__(16) bf16 o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(relu ? fmaxf(acc[c], 0.f) : acc[c]);
+    bf16* dst = (bf16*)out.p + p * out.ps + out.off;
+    *(uint4*)dst = *(const uint4*)o;
+    *(uint4*)(dst + 8) = *(const uint4*)(o + 8);
+  }
+}
+
+// NHWC head output [N][P][cout] -> planar [N][cout][P] (P = pixels): one
+// thread per pixel reads its C contiguous values; the planar stores of a warp
+// are contiguous
 __global__ void k_unpack_out(const float* y, float* out, long long P, int C, int N) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * C * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * N;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i % P;
-    const int c = (int)((i / P) % C);
-    const long long n = i / (P * C);
-    out[i] = y[(n * P + p) * C + c];
+    const long long n = i / P, p = i % P;
+    for (int c = 0; c < C; ++c) out[(n * C + c) * P + p] = y[i * C + c];
   }
 }
 
@@ -489,21 +543,17 @@ __global__ void k_targets(const float* m, const float* wr, const float* rms, flo
   }
 }
 
-// The warm start in input units: m0 [N][C-1][P] and wr0 [N][P] from the NHWC head output.
+// The warm start in input units: m0 [N][C-1][P] and wr0 [N][P] from the NHWC
+// head output (one thread per pixel, as k_unpack_out).
 __global__ void k_predict_out(const float* y, const float* rms, float* m0, float* wr0,
                               long long P, int C, int N, float wr_pow) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * C * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * N;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i % P;
-    const int c = (int)((i / P) % C);
-    const long long n = i / (P * C);
+    const long long n = i / P, p = i % P;
     const float r = rms[n];
-    const float v = y[(n * P + p) * C + c];
-    if (c < C - 1) {
-      if (m0) m0[(n * (C - 1) + c) * P + p] = v * r;
-    } else if (wr0) {
-      wr0[n * P + p] = expf(v) * powf(r, wr_pow);
-    }
+    if (m0)
+      for (int c = 0; c < C - 1; ++c) m0[(n * (C - 1) + c) * P + p] = y[i * C + c] * r;
+    if (wr0) wr0[n * P + p] = expf(y[i * C + C - 1]) * powf(r, wr_pow);
   }
 }
 
@@ -537,6 +587,7 @@ struct ashrt_unet {
   float *y, *gy, *g1a, *gcat1, *gp1, *g2a, *gcat2, *gp2, *g3a, *gcat3, *gp3, *gba, *gbb, *gd3a,
       *gd3b, *gd2a, *gd2b, *gd1a, *gd1b;
   float *rms, *lam;
+  double* rmsacc;
   double* loss;
   std::vector<float> lam_h;
 };
@@ -578,6 +629,287 @@ void conv(Tensor in, Tensor mask, const bf16* w, const float* bias, Tensor out, 
   count_launches(1);
 }
 
+// ---------------------------------------------------------------------------
+// 5th-generation tensor-core (tcgen05) forward convolution.  M = 128 pixels of
+// one image row (one TMEM lane each), N = the layer's output channels rounded
+// up to 16 (one tile, <= 256 FP32 TMEM columns), K = 16 input channels per
+// MMA, one MMA per tap, accumulated in TMEM over taps and channel chunks.
+// Per 16-channel chunk the CTA stages, in the canonical K-major no-swizzle
+// layout of 8-row x 16-byte core matrices,
+//   A: [dy][2 channel octets][130 pixels][8 channels]  (a tap's A operand
+//      starts dx pixels in: rows 16 B apart, next 8 pixels at +128 B = SBO,
+//      next channel octet at +130 x 16 B = LBO)
+//   B: [tap][2 octets][NT channels][8 input channels]  (SBO 128 B, LBO NT x 16 B)
+// with cp.async into one of two stages, so that the copies of the next chunk
+// overlap the MMAs of the current one; one thread issues the taps' MMAs and
+// commits them to the stage's mbarrier, which is waited on (bounded) before
+// that stage is refilled.  The epilogue reads the accumulators with tcgen05.ld
+// (warps w and w + 4: lanes 32 (w mod 4)..+31, alternate column groups) and
+// fuses bias, ReLU and the store.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);   // version 1, no swizzle
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Waits for the barrier phase; false after about a second.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < (1 << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (i > 64) __nanosleep(256);
+  }
+  return false;
+}
+
+struct TcConvArgs {
+  Tensor in;             // bf16 NHWC slice, ps and off multiples of 8
+  const bf16* w;         // [K*K][Cout][Cin]
+  const float* bias;     // [Cout]
+  Tensor out;            // bf16 or fp32 NHWC slice
+  int N, H, W, Cin, Cout, relu;
+  int* err;              // set to 1 if the MMA completion wait ran out
+};
+
+__device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+template <int K, int NT, typename TO>
+__global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
+  constexpr int R = K / 2, PW = 128 + 2 * R, TAPS = K * K, T = 256;
+  constexpr int NCOL = NT <= 32 ? 32 : NT <= 64 ? 64 : NT <= 128 ? 128 : 256;
+  constexpr uint32_t A_PLANE = PW * 16, B_PLANE = NT * 16;       // bytes per channel octet
+  constexpr uint32_t A_BYTES = K * 2 * A_PLANE, B_BYTES = TAPS * 2 * B_PLANE;
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);        // F32 += BF16 x BF16, M 128
+  extern __shared__ __align__(128) unsigned char smt[];
+  // two stages of [A | B]; then two mbarriers (one per stage) and the TMEM slot
+  uint64_t* bar = (uint64_t*)(smt + 2 * (A_BYTES + B_BYTES));
+  uint32_t* tslot = (uint32_t*)(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int xt = (a.W + 127) / 128;
+  const int row = blockIdx.x / xt;
+  const int x0 = (blockIdx.x % xt) * 128;
+  const int n = row / a.H, y = row % a.H;
+  const bf16* in = (const bf16*)a.in.p;
+  const int nch = a.Cin / 16;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_addr(tslot)),
+                 "r"((uint32_t)NCOL));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar + 1)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  // asynchronous copies of channel chunk c into stage st (zero-filled outside the image)
+  auto stage = [&](int c, int st) {
+    unsigned char* As = smt + st * (A_BYTES + B_BYTES);
+    unsigned char* Bs = As + A_BYTES;
+    const int ci0 = c * 16;
+    for (int e = tid; e < K * PW * 2; e += T) {
+      const int o = e % 2, px = (e / 2) % PW, r = e / (2 * PW);
+      const int yy = y + r - R, xx = x0 + px - R;
+      const bool ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+      const bf16* src = ok ? in + (((long long)n * a.H + yy) * a.W + xx) * a.in.ps + a.in.off +
+                                 ci0 + 8 * o
+                           : in;
+      cp16(As + (r * 2 + o) * A_PLANE + px * 16, src, ok);
+    }
+    for (int e = tid; e < TAPS * NT * 2; e += T) {
+      const int o = e % 2, co = (e / 2) % NT, tap = e / (2 * NT);
+      const bool ok = co < a.Cout;
+      const bf16* src = ok ? a.w + ((long long)tap * a.Cout + co) * a.Cin + ci0 + 8 * o : a.w;
+      cp16(Bs + (tap * 2 + o) * B_PLANE + co * 16, src, ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+
+  uint32_t uses[2] = {0u, 0u};   // completed MMA batches per stage (barrier parity)
+  bool failed = false;
+  stage(0, 0);
+  for (int c = 0; c < nch; ++c) {
+    const int st = c & 1;
+    if (c + 1 < nch) {
+      // stage c+1 goes into the buffers of chunk c-1: wait for its MMAs first
+      if (c >= 1) {
+        const bool ok = tc_wait(bar + (st ^ 1), uses[st ^ 1] & 1u);
+        uses[st ^ 1] += 1u;
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          break;
+        }
+      }
+      stage(c + 1, st ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const unsigned char* As = smt + st * (A_BYTES + B_BYTES);
+      const unsigned char* Bs = As + A_BYTES;
+#pragma unroll
+      for (int tap = 0; tap < TAPS; ++tap) {
+        const int dy = tap / K, dx = tap % K;
+        const uint64_t ad = umma_desc(smem_addr(As + dy * 2 * A_PLANE + dx * 16), A_PLANE, 128);
+        const uint64_t bd = umma_desc(smem_addr(Bs + tap * 2 * B_PLANE), B_PLANE, 128);
+        const uint32_t acc = (c > 0 || tap > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              smem_addr(bar + st))
+          : "memory");
+    }
+  }
+  if (!failed) {
+    // the last batch's completion implies all earlier ones (same issuing thread)
+    const int st = (nch - 1) & 1;
+    const bool ok = tc_wait(bar + st, uses[st] & 1u);
+    if (__syncthreads_or(!ok)) failed = true;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+  if (!failed) {
+    // epilogue: thread = pixel (TMEM lane of its warp quarter); warps w and
+    // w + 4 share lanes and split the 16-column groups
+    const int lane_base = (warp & 3) * 32;
+    const int xx = x0 + lane_base + (tid & 31);
+    const long long pix = ((long long)n * a.H + y) * a.W + xx;
+    TO* out = (TO*)a.out.p;
+    for (int c0 = (warp >> 2) * 16; c0 < NT; c0 += 32) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (xx < a.W) {
+        if (sizeof(TO) == 2 && c0 + 16 <= a.Cout && ((a.out.ps | a.out.off) & 7) == 0) {
+          __align__(16) bf16 o[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float v = __uint_as_float(r[j]) + a.bias[c0 + j];
+            o[j] = __float2bfloat16(a.relu ? fmaxf(v, 0.f) : v);
+          }
+          bf16* dst = (bf16*)out + pix * a.out.ps + a.out.off + c0;
+          *(uint4*)dst = *(const uint4*)o;
+          *(uint4*)(dst + 8) = *(const uint4*)(o + 8);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int co = c0 + j;
+            if (co < a.Cout) {
+              float v = __uint_as_float(r[j]) + a.bias[co];
+              if (a.relu) v = fmaxf(v, 0.f);
+              st_f(out, pix * a.out.ps + a.out.off + co, v);
+            }
+          }
+        }
+      }
+    }
+  } else if (tid == 0 && a.err) {
+    atomicExch(a.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"((uint32_t)NCOL));
+  }
+}
+
+template <int K, int NT, typename TO>
+void conv_tc_v(const TcConvArgs& a, cudaStream_t s) {
+  constexpr int R = K / 2, PW = 128 + 2 * R;
+  constexpr int NCOL = NT <= 32 ? 32 : NT <= 64 ? 64 : NT <= 128 ? 128 : 256;
+  // at most 512 / NCOL CTAs per SM may hold TMEM at once: request enough
+  // shared memory that no more are resident (228 KB per SM, 1 KB reserved
+  // per CTA), so that no CTA waits in tcgen05.alloc
+  const size_t need = 2 * ((size_t)K * 2 * PW * 16 + (size_t)K * K * 2 * NT * 16) + 32;
+  const size_t floor_b = 233472 / (512 / NCOL + 1);
+  const size_t smem = std::max(need, floor_b);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv_tc<K, NT, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
+  dim3 grid((unsigned)((long long)a.N * a.H * ((a.W + 127) / 128)));
+  k_conv_tc<K, NT, TO><<<grid, 256, smem, s>>>(a);
+  count_launches(1);
+}
+
+// tcgen05 forward convolution for the layer sizes of the network; false if the
+// output-channel tile is not one of the compiled ones (the caller then uses
+// the mma.sync kernel)
+template <int K, typename TO>
+bool conv_tc(Tensor in, const bf16* w, const float* bias, Tensor out, int N, int H, int W,
+             int Cin, int Cout, int relu, int* err, cudaStream_t s) {
+  if (Cin % 16 != 0 || in.ps % 8 != 0 || in.off % 8 != 0) return false;
+  TcConvArgs a;
+  a.in = in;
+  a.w = w;
+  a.bias = bias;
+  a.out = out;
+  a.N = N;
+  a.H = H;
+  a.W = W;
+  a.Cin = Cin;
+  a.Cout = Cout;
+  a.relu = relu;
+  a.err = err;
+  const int nt = (Cout + 15) / 16 * 16;
+  if constexpr (K == 3) {
+    switch (nt) {
+      case 16: conv_tc_v<3, 16, TO>(a, s); return true;
+      case 48: conv_tc_v<3, 48, TO>(a, s); return true;
+      case 96: conv_tc_v<3, 96, TO>(a, s); return true;
+      case 192: conv_tc_v<3, 192, TO>(a, s); return true;
+      default: return false;
+    }
+  } else {
+    switch (nt) {
+      case 16: conv_tc_v<1, 16, TO>(a, s); return true;
+      case 32: conv_tc_v<1, 32, TO>(a, s); return true;
+      case 48: conv_tc_v<1, 48, TO>(a, s); return true;
+      default: return false;
+    }
+  }
+}
+
 template <int K, int KC, int NB, typename TO>
 void conv_mma_v(const MmaConvArgs& a, cudaStream_t s) {
   constexpr int R = K / 2, PW = 128 + 2 * R, LDA = KC + 8;
@@ -598,7 +930,8 @@ void conv_mma_v(const MmaConvArgs& a, cudaStream_t s) {
 // output-channel tile from the layer's sizes.
 template <int K, typename TO>
 void conv_mma(Tensor in, const bf16* w, const float* bias, Tensor out, int N, int H, int W,
-              int Cin, int Cout, int relu, cudaStream_t s) {
+              int Cin, int Cout, int relu, cudaStream_t s, int* err = nullptr) {
+  if (conv_tc<K, TO>(in, w, bias, out, N, H, W, Cin, Cout, relu, err, s)) return;
   MmaConvArgs a;
   a.in = in;
   a.w = w;
@@ -658,6 +991,14 @@ void wgrad(Tensor in, Tensor g, Tensor mask, float* gw, float* gb, int N, int H,
   count_launches(1);
 }
 
+// rms[g] of the n input gathers x [n][per]
+void compute_rms(ashrt_unet* u, const float* x, long long per, int n, cudaStream_t s) {
+  cudaMemsetAsync(u->rmsacc, 0, sizeof(double) * n, s);
+  k_sumsq<<<dim3(64, n), 256, 0, s>>>(x, per, u->rmsacc);
+  k_rms_fin<<<(n + 127) / 128, 128, 0, s>>>(u->rmsacc, per, u->rms, n);
+  count_launches(2);
+}
+
 // Forward pass on `n` images already packed in u->x; writes u->y (NHWC fp32).
 void net_forward(ashrt_unet* u, int n, cudaStream_t s) {
   const int H = u->H, W = u->W, c0 = u->ch[0], c1 = u->ch[1], c2 = u->ch[2], c3 = u->ch[3];
@@ -666,7 +1007,8 @@ void net_forward(ashrt_unet* u, int n, cudaStream_t s) {
   auto B = [&](int i) { return u->w + L[i].b_off; };
   auto grid = [&](long long cnt) { return grid1d(cnt); };
   // encoder
-  conv<3, bf16, bf16>(T_(u->x, 1), none, L[0].wf, B(0), T_(u->e1a, c0), n, H, W, 1, c0, 1, s);
+  k_conv_first<<<grid((long long)n * H * W), 256, 0, s>>>(u->x, L[0].wf, B(0), T_(u->e1a, c0), n,
+                                                          H, W, 1);
   conv_mma<3, bf16>(T_(u->e1a, c0), L[1].wn, B(1), T_(u->cat1, c1 + c0, c1), n, H, W, c0, c0, 1, s);
   k_pool<<<grid((long long)n * H * W / 4 * c0), 256, 0, s>>>(T_(u->cat1, c1 + c0, c1), T_(u->p1, c0), n, H, W, c0);
   conv_mma<3, bf16>(T_(u->p1, c0), L[2].wn, B(2), T_(u->e2a, c1), n, H / 2, W / 2, c0, c1, 1, s);
@@ -678,17 +1020,17 @@ void net_forward(ashrt_unet* u, int n, cudaStream_t s) {
   conv_mma<3, bf16>(T_(u->p3, c2), L[6].wn, B(6), T_(u->ba, c3), n, H / 8, W / 8, c2, c3, 1, s);
   conv_mma<3, bf16>(T_(u->ba, c3), L[7].wn, B(7), T_(u->bb, c3), n, H / 8, W / 8, c3, c3, 1, s);
   // decoder
-  k_up<<<grid((long long)n * H * W / 16 * c3), 256, 0, s>>>(T_(u->bb, c3), T_(u->cat3, c3 + c2, 0), n, H / 4, W / 4, c3);
+  k_up<<<grid((long long)n * H * W / 16 * c3 / 8), 256, 0, s>>>(T_(u->bb, c3), T_(u->cat3, c3 + c2, 0), n, H / 4, W / 4, c3);
   conv_mma<3, bf16>(T_(u->cat3, c3 + c2), L[8].wn, B(8), T_(u->d3a, c2), n, H / 4, W / 4, c3 + c2, c2, 1, s);
   conv_mma<3, bf16>(T_(u->d3a, c2), L[9].wn, B(9), T_(u->d3b, c2), n, H / 4, W / 4, c2, c2, 1, s);
-  k_up<<<grid((long long)n * H * W / 4 * c2), 256, 0, s>>>(T_(u->d3b, c2), T_(u->cat2, c2 + c1, 0), n, H / 2, W / 2, c2);
+  k_up<<<grid((long long)n * H * W / 4 * c2 / 8), 256, 0, s>>>(T_(u->d3b, c2), T_(u->cat2, c2 + c1, 0), n, H / 2, W / 2, c2);
   conv_mma<3, bf16>(T_(u->cat2, c2 + c1), L[10].wn, B(10), T_(u->d2a, c1), n, H / 2, W / 2, c2 + c1, c1, 1, s);
   conv_mma<3, bf16>(T_(u->d2a, c1), L[11].wn, B(11), T_(u->d2b, c1), n, H / 2, W / 2, c1, c1, 1, s);
-  k_up<<<grid((long long)n * H * W * c1), 256, 0, s>>>(T_(u->d2b, c1), T_(u->cat1, c1 + c0, 0), n, H, W, c1);
+  k_up<<<grid((long long)n * H * W * c1 / 8), 256, 0, s>>>(T_(u->d2b, c1), T_(u->cat1, c1 + c0, 0), n, H, W, c1);
   conv_mma<3, bf16>(T_(u->cat1, c1 + c0), L[12].wn, B(12), T_(u->d1a, c0), n, H, W, c1 + c0, c0, 1, s);
   conv_mma<3, bf16>(T_(u->d1a, c0), L[13].wn, B(13), T_(u->d1b, c0), n, H, W, c0, c0, 1, s);
   conv_mma<1, float>(T_(u->d1b, c0), L[14].wn, B(14), T_(u->y, u->cout), n, H, W, c0, u->cout, 0, s);
-  count_launches(6);
+  count_launches(7);   // pools, upsamplings, first layer
 }
 
 // Backward pass from u->gy (NHWC fp32); accumulates parameter gradients in u->g.
@@ -844,6 +1186,7 @@ ashrt_status ashrt_unet_create(ashrt_unet** out, int H, int W, int out_channels,
   A(&u->gd1a, P0 * c0);
   A(&u->gd1b, P0 * c0);
   A(&u->rms, max_batch);
+  A(&u->rmsacc, max_batch);
   A(&u->lam, out_channels);
   A(&u->loss, 1);
   if (e != cudaSuccess) {
@@ -934,11 +1277,11 @@ ashrt_status ashrt_unet_forward(ashrt_unet* u, const float* x, float* y, int n, 
   }
   cudaStream_t s = (cudaStream_t)stream;
   const long long per = (long long)u->H * u->W;
-  k_rms<<<n, 256, 0, s>>>(x, per, u->rms);
+  compute_rms(u, x, per, n, s);
   k_pack_in<<<grid1d(per * n), 256, 0, s>>>(x, u->rms, u->x, per, n);
-  count_launches(2);
+  count_launches(1);
   net_forward(u, n, s);
-  k_unpack_out<<<grid1d(per * u->cout * n), 256, 0, s>>>(u->y, y, per, u->cout, n);
+  k_unpack_out<<<grid1d(per * n), 256, 0, s>>>(u->y, y, per, u->cout, n);
   count_launches(1);
   if (rescale) {
     k_rescale_out<<<grid1d(per * u->cout * n), 256, 0, s>>>(y, u->rms, per, u->cout, n,
@@ -975,9 +1318,9 @@ ashrt_status ashrt_unet_train_step(ashrt_unet* u, const float* x, const float* t
   }
   cudaMemsetAsync(u->loss, 0, sizeof(double), s);
   cudaMemsetAsync(u->g, 0, u->nparam * 4, s);
-  k_rms<<<n, 256, 0, s>>>(x, per, u->rms);
+  compute_rms(u, x, per, n, s);
   k_pack_in<<<grid1d(per * n), 256, 0, s>>>(x, u->rms, u->x, per, n);
-  count_launches(2);
+  count_launches(1);
   net_forward(u, n, s);
   k_mse<<<grid1d(per * u->cout * n), 256, 0, s>>>(u->y, target, u->lam, u->gy, per, u->cout, n,
                                                   u->loss);
@@ -1013,10 +1356,10 @@ ashrt_status ashrt_unet_targets(ashrt_unet* u, const float* x, const float* m, c
   }
   cudaStream_t s = (cudaStream_t)stream;
   const long long per = (long long)u->H * u->W;
-  k_rms<<<n, 256, 0, s>>>(x, per, u->rms);
+  compute_rms(u, x, per, n, s);
   k_targets<<<grid1d(per * u->cout * n), 256, 0, s>>>(m, wr, u->rms, t, per, u->cout, n,
                                                       0.5f * (p - 2.f));
-  count_launches(2);
+  count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error("ashrt_unet_targets: %s", cudaGetErrorString(e));
@@ -1033,11 +1376,11 @@ ashrt_status ashrt_unet_predict(ashrt_unet* u, const float* x, float* m0, float*
   }
   cudaStream_t s = (cudaStream_t)stream;
   const long long per = (long long)u->H * u->W;
-  k_rms<<<n, 256, 0, s>>>(x, per, u->rms);
+  compute_rms(u, x, per, n, s);
   k_pack_in<<<grid1d(per * n), 256, 0, s>>>(x, u->rms, u->x, per, n);
-  count_launches(2);
+  count_launches(1);
   net_forward(u, n, s);
-  k_predict_out<<<grid1d(per * u->cout * n), 256, 0, s>>>(u->y, u->rms, m0, wr0, per, u->cout,
+  k_predict_out<<<grid1d(per * n), 256, 0, s>>>(u->y, u->rms, m0, wr0, per, u->cout,
                                                           n, 0.5f * (p - 2.f));
   count_launches(1);
   cudaError_t e = cudaGetLastError();

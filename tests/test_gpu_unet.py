@@ -64,11 +64,12 @@ def _normalised(x):
 Q = unet.bf16_round
 
 
-@pytest.mark.parametrize("H,W,n", [(16, 32, 2), (24, 200, 2)])
-def test_forward_matches_fp64_network(lib, H, W, n):
+@pytest.mark.parametrize("H,W,n,cout", [(16, 32, 2, 5), (24, 200, 2, 5), (16, 64, 1, 60)])
+def test_forward_matches_fp64_network(lib, H, W, n, cout):
+    """cout 5 and the hidden layers run on the tcgen05 kernel; a 60-channel
+    head (a 64-wide tile) on the mma.sync kernel."""
     import torch
     from paper_1711_10214_gb300 import ashrt
-    cout = 5
     specs, p, x, _ = _setup(H, W, cout, n, 31)
     net = ashrt.UNet(H, W, cout, max_batch=n, params=_flat(p, specs))
     assert net.n_params == sum(co * ci * k * k + co for _, ci, co, k in specs)
