@@ -543,17 +543,18 @@ __global__ void k_targets(const float* m, const float* wr, const float* rms, flo
   }
 }
 
-// The warm start in input units: m0 [N][C-1][P] and wr0 [N][P] from the NHWC
-// head output (one thread per pixel, as k_unpack_out).
+// The warm start in input units: m0 [N][C-1][P] and wr0 [N][P] from the
+// planar head output [N][C][P].
 __global__ void k_predict_out(const float* y, const float* rms, float* m0, float* wr0,
                               long long P, int C, int N, float wr_pow) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * N;
        i += (long long)gridDim.x * blockDim.x) {
     const long long n = i / P, p = i % P;
     const float r = rms[n];
+    const float* yn = y + n * C * P + p;
     if (m0)
-      for (int c = 0; c < C - 1; ++c) m0[(n * (C - 1) + c) * P + p] = y[i * C + c] * r;
-    if (wr0) wr0[n * P + p] = expf(y[i * C + C - 1]) * powf(r, wr_pow);
+      for (int c = 0; c < C - 1; ++c) m0[(n * (C - 1) + c) * P + p] = yn[(long long)c * P] * r;
+    if (wr0) wr0[n * P + p] = expf(yn[(long long)(C - 1) * P]) * powf(r, wr_pow);
   }
 }
 
@@ -678,6 +679,7 @@ struct TcConvArgs {
   Tensor out;            // bf16 or fp32 NHWC slice
   int N, H, W, Cin, Cout, relu;
   int* err;              // set to 1 if the MMA completion wait ran out
+  int planar = 0;        // 1: out.p is planar [N][Cout][H*W] (ps, off unused)
 };
 
 __device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
@@ -686,12 +688,14 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
                : "memory");
 }
 
-template <int K, int NT, typename TO>
+template <int K, int NT, int RR, typename TO>
 __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
-  constexpr int R = K / 2, PW = 128 + 2 * R, TAPS = K * K, T = 256;
-  constexpr int NCOL = NT <= 32 ? 32 : NT <= 64 ? 64 : NT <= 128 ? 128 : 256;
+  constexpr int R = K / 2, PW = 128 + 2 * R, TAPS = K * K, T = 256, ROWS = RR + 2 * R;
+  constexpr int DS = (NT + 31) / 32 * 32;        // TMEM columns per output row
+  constexpr int NCOL = RR * DS <= 32 ? 32 : RR * DS <= 64 ? 64 : RR * DS <= 128 ? 128 : 256;
+  static_assert(RR * DS <= 256, "TMEM tile");
   constexpr uint32_t A_PLANE = PW * 16, B_PLANE = NT * 16;       // bytes per channel octet
-  constexpr uint32_t A_BYTES = K * 2 * A_PLANE, B_BYTES = TAPS * 2 * B_PLANE;
+  constexpr uint32_t A_BYTES = ROWS * 2 * A_PLANE, B_BYTES = TAPS * 2 * B_PLANE;
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                              ((uint32_t)(128 >> 4) << 24);        // F32 += BF16 x BF16, M 128
   extern __shared__ __align__(128) unsigned char smt[];
@@ -699,10 +703,10 @@ __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
   uint64_t* bar = (uint64_t*)(smt + 2 * (A_BYTES + B_BYTES));
   uint32_t* tslot = (uint32_t*)(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int xt = (a.W + 127) / 128;
-  const int row = blockIdx.x / xt;
+  const int xt = (a.W + 127) / 128, yt = (a.H + RR - 1) / RR;
   const int x0 = (blockIdx.x % xt) * 128;
-  const int n = row / a.H, y = row % a.H;
+  const int rb = blockIdx.x / xt;                 // n * yt + row block
+  const int n = rb / yt, y0 = (rb % yt) * RR;
   const bf16* in = (const bf16*)a.in.p;
   const int nch = a.Cin / 16;
 
@@ -727,9 +731,9 @@ __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
     unsigned char* As = smt + st * (A_BYTES + B_BYTES);
     unsigned char* Bs = As + A_BYTES;
     const int ci0 = c * 16;
-    for (int e = tid; e < K * PW * 2; e += T) {
+    for (int e = tid; e < ROWS * PW * 2; e += T) {
       const int o = e % 2, px = (e / 2) % PW, r = e / (2 * PW);
-      const int yy = y + r - R, xx = x0 + px - R;
+      const int yy = y0 + r - R, xx = x0 + px - R;
       const bool ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
       const bf16* src = ok ? in + (((long long)n * a.H + yy) * a.W + xx) * a.in.ps + a.in.off +
                                  ci0 + 8 * o
@@ -773,15 +777,20 @@ __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
       const unsigned char* As = smt + st * (A_BYTES + B_BYTES);
       const unsigned char* Bs = As + A_BYTES;
 #pragma unroll
-      for (int tap = 0; tap < TAPS; ++tap) {
-        const int dy = tap / K, dx = tap % K;
-        const uint64_t ad = umma_desc(smem_addr(As + dy * 2 * A_PLANE + dx * 16), A_PLANE, 128);
-        const uint64_t bd = umma_desc(smem_addr(Bs + tap * 2 * B_PLANE), B_PLANE, 128);
-        const uint32_t acc = (c > 0 || tap > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+      for (int r = 0; r < RR; ++r) {
+#pragma unroll
+        for (int tap = 0; tap < TAPS; ++tap) {
+          const int dy = tap / K, dx = tap % K;
+          const uint64_t ad =
+              umma_desc(smem_addr(As + (r + dy) * 2 * A_PLANE + dx * 16), A_PLANE, 128);
+          const uint64_t bd = umma_desc(smem_addr(Bs + tap * 2 * B_PLANE), B_PLANE, 128);
+          const uint32_t acc = (c > 0 || tap > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                  tmem + (uint32_t)(r * DS)),
+              "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+        }
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
@@ -800,28 +809,43 @@ __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
 
   if (!failed) {
     // epilogue: thread = pixel (TMEM lane of its warp quarter); warps w and
-    // w + 4 share lanes and split the 16-column groups
+    // w + 4 share lanes and split the (row, 16-column) groups
     const int lane_base = (warp & 3) * 32;
     const int xx = x0 + lane_base + (tid & 31);
-    const long long pix = ((long long)n * a.H + y) * a.W + xx;
     TO* out = (TO*)a.out.p;
-    for (int c0 = (warp >> 2) * 16; c0 < NT; c0 += 32) {
-      uint32_t r[16];
+    constexpr int G = NT / 16;
+    for (int gi = warp >> 2; gi < RR * G; gi += 2) {
+      const int r = gi / G, c0 = (gi % G) * 16;
+      uint32_t v[16];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
           "%11, %12, %13, %14, %15}, [%16];\n"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c0));
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(r * DS + c0)));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (xx < a.W) {
-        if (sizeof(TO) == 2 && c0 + 16 <= a.Cout && ((a.out.ps | a.out.off) & 7) == 0) {
+      const int y = y0 + r;
+      if (xx < a.W && y < a.H) {
+        const long long pix = ((long long)n * a.H + y) * a.W + xx;
+        if (a.planar) {
+          // planar output [N][Cout][H*W]: the stores of a warp are contiguous
+          const long long P = (long long)a.H * a.W, p = (long long)y * a.W + xx;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int co = c0 + j;
+            if (co < a.Cout) {
+              float f = __uint_as_float(v[j]) + a.bias[co];
+              if (a.relu) f = fmaxf(f, 0.f);
+              st_f(out, ((long long)n * a.Cout + co) * P + p, f);
+            }
+          }
+        } else if (sizeof(TO) == 2 && c0 + 16 <= a.Cout && ((a.out.ps | a.out.off) & 7) == 0) {
           __align__(16) bf16 o[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            float v = __uint_as_float(r[j]) + a.bias[c0 + j];
-            o[j] = __float2bfloat16(a.relu ? fmaxf(v, 0.f) : v);
+            float f = __uint_as_float(v[j]) + a.bias[c0 + j];
+            o[j] = __float2bfloat16(a.relu ? fmaxf(f, 0.f) : f);
           }
           bf16* dst = (bf16*)out + pix * a.out.ps + a.out.off + c0;
           *(uint4*)dst = *(const uint4*)o;
@@ -831,9 +855,9 @@ __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
           for (int j = 0; j < 16; ++j) {
             const int co = c0 + j;
             if (co < a.Cout) {
-              float v = __uint_as_float(r[j]) + a.bias[co];
-              if (a.relu) v = fmaxf(v, 0.f);
-              st_f(out, pix * a.out.ps + a.out.off + co, v);
+              float f = __uint_as_float(v[j]) + a.bias[co];
+              if (a.relu) f = fmaxf(f, 0.f);
+              st_f(out, pix * a.out.ps + a.out.off + co, f);
             }
           }
         }
@@ -851,24 +875,24 @@ __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
   }
 }
 
-template <int K, int NT, typename TO>
+template <int K, int NT, int RR, typename TO>
 void conv_tc_v(const TcConvArgs& a, cudaStream_t s) {
-  constexpr int R = K / 2, PW = 128 + 2 * R;
-  constexpr int NCOL = NT <= 32 ? 32 : NT <= 64 ? 64 : NT <= 128 ? 128 : 256;
+  constexpr int R = K / 2, PW = 128 + 2 * R, ROWS = RR + 2 * R, DS = (NT + 31) / 32 * 32;
+  constexpr int NCOL = RR * DS <= 32 ? 32 : RR * DS <= 64 ? 64 : RR * DS <= 128 ? 128 : 256;
   // at most 512 / NCOL CTAs per SM may hold TMEM at once: request enough
   // shared memory that no more are resident (228 KB per SM, 1 KB reserved
   // per CTA), so that no CTA waits in tcgen05.alloc
-  const size_t need = 2 * ((size_t)K * 2 * PW * 16 + (size_t)K * K * 2 * NT * 16) + 32;
+  const size_t need = 2 * ((size_t)ROWS * 2 * PW * 16 + (size_t)K * K * 2 * NT * 16) + 32;
   const size_t floor_b = 233472 / (512 / NCOL + 1);
   const size_t smem = std::max(need, floor_b);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_conv_tc<K, NT, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_conv_tc<K, NT, RR, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr = true;
   }
-  dim3 grid((unsigned)((long long)a.N * a.H * ((a.W + 127) / 128)));
-  k_conv_tc<K, NT, TO><<<grid, 256, smem, s>>>(a);
+  dim3 grid((unsigned)((long long)a.N * ((a.H + RR - 1) / RR) * ((a.W + 127) / 128)));
+  k_conv_tc<K, NT, RR, TO><<<grid, 256, smem, s>>>(a);
   count_launches(1);
 }
 
@@ -877,9 +901,10 @@ void conv_tc_v(const TcConvArgs& a, cudaStream_t s) {
 // the mma.sync kernel)
 template <int K, typename TO>
 bool conv_tc(Tensor in, const bf16* w, const float* bias, Tensor out, int N, int H, int W,
-             int Cin, int Cout, int relu, int* err, cudaStream_t s) {
+             int Cin, int Cout, int relu, int* err, cudaStream_t s, int planar = 0) {
   if (Cin % 16 != 0 || in.ps % 8 != 0 || in.off % 8 != 0) return false;
   TcConvArgs a;
+  a.planar = planar;
   a.in = in;
   a.w = w;
   a.bias = bias;
@@ -894,17 +919,18 @@ bool conv_tc(Tensor in, const bf16* w, const float* bias, Tensor out, int N, int
   const int nt = (Cout + 15) / 16 * 16;
   if constexpr (K == 3) {
     switch (nt) {
-      case 16: conv_tc_v<3, 16, TO>(a, s); return true;
-      case 48: conv_tc_v<3, 48, TO>(a, s); return true;
-      case 96: conv_tc_v<3, 96, TO>(a, s); return true;
-      case 192: conv_tc_v<3, 192, TO>(a, s); return true;
+      // output rows per CTA: the staged input rows serve RR outputs (TMEM: RR x NT <= 256)
+      case 16: conv_tc_v<3, 16, 4, TO>(a, s); return true;
+      case 48: conv_tc_v<3, 48, 4, TO>(a, s); return true;
+      case 96: conv_tc_v<3, 96, 2, TO>(a, s); return true;
+      case 192: conv_tc_v<3, 192, 1, TO>(a, s); return true;
       default: return false;
     }
   } else {
     switch (nt) {
-      case 16: conv_tc_v<1, 16, TO>(a, s); return true;
-      case 32: conv_tc_v<1, 32, TO>(a, s); return true;
-      case 48: conv_tc_v<1, 48, TO>(a, s); return true;
+      case 16: conv_tc_v<1, 16, 1, TO>(a, s); return true;
+      case 32: conv_tc_v<1, 32, 1, TO>(a, s); return true;
+      case 48: conv_tc_v<1, 48, 1, TO>(a, s); return true;
       default: return false;
     }
   }
@@ -1000,7 +1026,9 @@ void compute_rms(ashrt_unet* u, const float* x, long long per, int n, cudaStream
 }
 
 // Forward pass on `n` images already packed in u->x; writes u->y (NHWC fp32).
-void net_forward(ashrt_unet* u, int n, cudaStream_t s) {
+// head_planar: write the head's output there as planar [n][cout][H*W]
+// (inference) instead of NHWC into u->y (training).
+void net_forward(ashrt_unet* u, int n, cudaStream_t s, float* head_planar = nullptr) {
   const int H = u->H, W = u->W, c0 = u->ch[0], c1 = u->ch[1], c2 = u->ch[2], c3 = u->ch[3];
   const Tensor none = T_(nullptr, 0);
   auto& L = u->L;
@@ -1029,7 +1057,16 @@ void net_forward(ashrt_unet* u, int n, cudaStream_t s) {
   k_up<<<grid((long long)n * H * W * c1 / 8), 256, 0, s>>>(T_(u->d2b, c1), T_(u->cat1, c1 + c0, 0), n, H, W, c1);
   conv_mma<3, bf16>(T_(u->cat1, c1 + c0), L[12].wn, B(12), T_(u->d1a, c0), n, H, W, c1 + c0, c0, 1, s);
   conv_mma<3, bf16>(T_(u->d1a, c0), L[13].wn, B(13), T_(u->d1b, c0), n, H, W, c0, c0, 1, s);
-  conv_mma<1, float>(T_(u->d1b, c0), L[14].wn, B(14), T_(u->y, u->cout), n, H, W, c0, u->cout, 0, s);
+  if (!head_planar || !conv_tc<1, float>(T_(u->d1b, c0), L[14].wn, B(14), T_(head_planar, 1), n, H,
+                                         W, c0, u->cout, 0, nullptr, s, 1)) {
+    conv_mma<1, float>(T_(u->d1b, c0), L[14].wn, B(14), T_(u->y, u->cout), n, H, W, c0, u->cout,
+                       0, s);
+    if (head_planar) {
+      k_unpack_out<<<grid1d((long long)H * W * n), 256, 0, s>>>(u->y, head_planar,
+                                                               (long long)H * W, u->cout, n);
+      count_launches(1);
+    }
+  }
   count_launches(7);   // pools, upsamplings, first layer
 }
 
@@ -1280,9 +1317,7 @@ ashrt_status ashrt_unet_forward(ashrt_unet* u, const float* x, float* y, int n, 
   compute_rms(u, x, per, n, s);
   k_pack_in<<<grid1d(per * n), 256, 0, s>>>(x, u->rms, u->x, per, n);
   count_launches(1);
-  net_forward(u, n, s);
-  k_unpack_out<<<grid1d(per * n), 256, 0, s>>>(u->y, y, per, u->cout, n);
-  count_launches(1);
+  net_forward(u, n, s, y);
   if (rescale) {
     k_rescale_out<<<grid1d(per * u->cout * n), 256, 0, s>>>(y, u->rms, per, u->cout, n,
                                                            0.5f * (p - 2.f));
@@ -1379,7 +1414,7 @@ ashrt_status ashrt_unet_predict(ashrt_unet* u, const float* x, float* m0, float*
   compute_rms(u, x, per, n, s);
   k_pack_in<<<grid1d(per * n), 256, 0, s>>>(x, u->rms, u->x, per, n);
   count_launches(1);
-  net_forward(u, n, s);
+  net_forward(u, n, s, u->y);
   k_predict_out<<<grid1d(per * n), 256, 0, s>>>(u->y, u->rms, m0, wr0, per, u->cout,
                                                           n, 0.5f * (p - 2.f));
   count_launches(1);
