@@ -41,8 +41,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="deblend", choices=["deblend", "ops"],
-                    help="ops: time forward+adjoint operator pairs only (profiling aid)")
+    ap.add_argument("--mode", default="deblend", choices=["deblend", "ops", "unet"],
+                    help="ops: forward+adjoint operator pairs only; unet: warm-start U-Net "
+                         "inference (profiling aids)")
     ap.add_argument("--batch", type=int, default=B,
                     help="gathers per call (the deblend workload is 64; smaller batches are "
                          "for profiling captures)")
@@ -342,10 +343,52 @@ def run_ops(args):
           flush=True)
 
 
+def _unet_flops(H, W, cout, ch=(16, 48, 96, 192)):
+    """Multiply-add flops of one U-Net forward on an H x W image (2 per MAC)."""
+    c0, c1, c2, c3 = ch
+    layers = [(1, c0, 3, 1), (c0, c0, 3, 1), (c0, c1, 3, 4), (c1, c1, 3, 4), (c1, c2, 3, 16),
+              (c2, c2, 3, 16), (c2, c3, 3, 64), (c3, c3, 3, 64), (c3 + c2, c2, 3, 16),
+              (c2, c2, 3, 16), (c2 + c1, c1, 3, 4), (c1, c1, 3, 4), (c1 + c0, c0, 3, 1),
+              (c0, c0, 3, 1), (c0, cout, 1, 1)]
+    return sum(2.0 * ci * co * k * k * H * W / div for ci, co, k, div in layers)
+
+
+def run_unet(args):
+    """Warm-start U-Net inference on 256 x 1024 gathers, 25 output channels (the
+    c5 warm start's network; a profiling aid, not the bench line)."""
+    import torch
+
+    from paper_1711_10214_gb300 import ashrt
+    dev = torch.device("cuda", 0)
+    nb, H, W, cout = args.batch, NX, NT, 25
+    net = ashrt.UNet(H, W, cout, max_batch=nb)
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = torch.randn((nb, H, W), device=dev, generator=g)
+    y = torch.empty((nb, cout, H, W), device=dev)
+    for _ in range(args.warmup):
+        net.forward(x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        net.forward(x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1000.0 / args.steps
+    f = _unet_flops(H, W, cout) * nb
+    print(json.dumps({"mode": "unet", "batch": nb, "ms_per_image": 1000.0 * t / nb,
+                      "images_per_s": nb / t, "tflops": f / t / 1e12,
+                      "gflop_per_image": f / nb / 1e9}), flush=True)
+    net.close()
+
+
 def main():
     args = _args()
     if args.mode == "ops":
         run_ops(args)
+        return
+    if args.mode == "unet":
+        run_unet(args)
         return
     if args.impl == "reference":
         run_reference(args)
