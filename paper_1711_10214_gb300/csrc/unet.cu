@@ -338,6 +338,33 @@ __global__ void k_conv_first(const bf16* x, const bf16* w, const float* bias, Te
   }
 }
 
+// The input of an input-gradient convolution on the tensor cores: the FP32
+// gradient of a layer's output, masked by the layer's ReLU (act > 0), rounded
+// to BF16 into a dense [pixels][C] buffer; 8 channels per thread (C, strides
+// and offsets multiples of 8).
+__global__ void k_gz_bf16(Tensor g, Tensor act, bf16* out, long long npix, int C) {
+  const int C8 = C / 8;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix * C8;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / C8;
+    const int c = (int)(i % C8) * 8;
+    const float4* gp = (const float4*)((const float*)g.p + p * g.ps + g.off + c);
+    const float4 g0 = gp[0], g1 = gp[1];
+    float v[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+    if (act.p) {
+      __align__(16) bf16 m[8];
+      *(uint4*)m = *(const uint4*)((const bf16*)act.p + p * act.ps + act.off + c);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (__bfloat162float(m[j]) <= 0.f) v[j] = 0.f;
+    }
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16(v[j]);
+    *(uint4*)(out + p * C + c) = *(const uint4*)o;
+  }
+}
+
 // NHWC head output [N][P][cout] -> planar [N][cout][P] (P = pixels): one
 // thread per pixel reads its C contiguous values; the planar stores of a warp
 // are contiguous
@@ -388,8 +415,10 @@ __global__ void k_adam(float* w, const float* g, float* m, float* v, long long n
 }
 
 // FP32 OIHW master -> BF16 [tap][ci][co] (forward, CUDA cores), flipped
-// [tap'][co][ci] (input gradient) and [tap][co][ci] (forward, tensor cores)
-__global__ void k_wconv(const float* w, bf16* wf, bf16* wt, bf16* wn, int co_n, int ci_n, int K) {
+// [tap'][co][ci] (input gradient, CUDA cores), [tap][co][ci] (forward, tensor
+// cores) and flipped [tap'][ci][co] (input gradient, tensor cores)
+__global__ void k_wconv(const float* w, bf16* wf, bf16* wt, bf16* wn, bf16* wtn, int co_n, int ci_n,
+                        int K) {
   const int total = co_n * ci_n * K * K;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int kx = i % K, ky = (i / K) % K, ci = (i / (K * K)) % ci_n, co = i / (K * K * ci_n);
@@ -398,6 +427,7 @@ __global__ void k_wconv(const float* w, bf16* wf, bf16* wt, bf16* wn, int co_n, 
     wf[((long long)tap * ci_n + ci) * co_n + co] = b;
     wt[((long long)tapf * co_n + co) * ci_n + ci] = b;
     wn[((long long)tap * co_n + co) * ci_n + ci] = b;
+    wtn[((long long)tapf * ci_n + ci) * co_n + co] = b;
   }
 }
 
@@ -562,7 +592,7 @@ __global__ void k_predict_out(const float* y, const float* rms, float* m0, float
 struct Layer {
   int ci, co, k;
   long long w_off, b_off;   // into the flat parameter buffer
-  bf16 *wf = nullptr, *wt = nullptr, *wn = nullptr;
+  bf16 *wf = nullptr, *wt = nullptr, *wn = nullptr, *wtn = nullptr;
 };
 
 int grid1d(long long n) {
@@ -589,6 +619,7 @@ struct ashrt_unet {
       *gd3b, *gd2a, *gd2b, *gd1a, *gd1b;
   float *rms, *lam;
   double* rmsacc;
+  bf16* gzb;   // BF16 masked output gradient of the layer being differentiated
   double* loss;
   std::vector<float> lam_h;
 };
@@ -707,6 +738,7 @@ __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
   const int x0 = (blockIdx.x % xt) * 128;
   const int rb = blockIdx.x / xt;                 // n * yt + row block
   const int n = rb / yt, y0 = (rb % yt) * RR;
+  const int co0 = blockIdx.y * NT;                // output-channel tile
   const bf16* in = (const bf16*)a.in.p;
   const int nch = a.Cin / 16;
 
@@ -741,10 +773,10 @@ __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
       cp16(As + (r * 2 + o) * A_PLANE + px * 16, src, ok);
     }
     for (int e = tid; e < TAPS * NT * 2; e += T) {
-      const int o = e % 2, co = (e / 2) % NT, tap = e / (2 * NT);
-      const bool ok = co < a.Cout;
-      const bf16* src = ok ? a.w + ((long long)tap * a.Cout + co) * a.Cin + ci0 + 8 * o : a.w;
-      cp16(Bs + (tap * 2 + o) * B_PLANE + co * 16, src, ok);
+      const int o = e % 2, c = (e / 2) % NT, tap = e / (2 * NT);
+      const bool ok = co0 + c < a.Cout;
+      const bf16* src = ok ? a.w + ((long long)tap * a.Cout + co0 + c) * a.Cin + ci0 + 8 * o : a.w;
+      cp16(Bs + (tap * 2 + o) * B_PLANE + c * 16, src, ok);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
@@ -828,38 +860,35 @@ __global__ void __launch_bounds__(256) k_conv_tc(TcConvArgs a) {
       const int y = y0 + r;
       if (xx < a.W && y < a.H) {
         const long long pix = ((long long)n * a.H + y) * a.W + xx;
+        const int cb = co0 + c0;                    // first output channel of the group
+        float f[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          f[j] = __uint_as_float(v[j]) + ((a.bias && cb + j < a.Cout) ? a.bias[cb + j] : 0.f);
+          if (a.relu) f[j] = fmaxf(f[j], 0.f);
+        }
+        const bool whole = cb + 16 <= a.Cout;
         if (a.planar) {
           // planar output [N][Cout][H*W]: the stores of a warp are contiguous
           const long long P = (long long)a.H * a.W, p = (long long)y * a.W + xx;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int co = c0 + j;
-            if (co < a.Cout) {
-              float f = __uint_as_float(v[j]) + a.bias[co];
-              if (a.relu) f = fmaxf(f, 0.f);
-              st_f(out, ((long long)n * a.Cout + co) * P + p, f);
-            }
-          }
-        } else if (sizeof(TO) == 2 && c0 + 16 <= a.Cout && ((a.out.ps | a.out.off) & 7) == 0) {
+          for (int j = 0; j < 16; ++j)
+            if (cb + j < a.Cout) st_f(out, ((long long)n * a.Cout + cb + j) * P + p, f[j]);
+        } else if (sizeof(TO) == 2 && whole && ((a.out.ps | a.out.off) & 7) == 0) {
           __align__(16) bf16 o[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            float f = __uint_as_float(v[j]) + a.bias[c0 + j];
-            o[j] = __float2bfloat16(a.relu ? fmaxf(f, 0.f) : f);
-          }
-          bf16* dst = (bf16*)out + pix * a.out.ps + a.out.off + c0;
+          for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(f[j]);
+          bf16* dst = (bf16*)out + pix * a.out.ps + a.out.off + cb;
           *(uint4*)dst = *(const uint4*)o;
           *(uint4*)(dst + 8) = *(const uint4*)(o + 8);
+        } else if (sizeof(TO) == 4 && whole && ((a.out.ps | a.out.off) & 3) == 0) {
+          float4* dst = (float4*)((float*)out + pix * a.out.ps + a.out.off + cb);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
         } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int co = c0 + j;
-            if (co < a.Cout) {
-              float f = __uint_as_float(v[j]) + a.bias[co];
-              if (a.relu) f = fmaxf(f, 0.f);
-              st_f(out, pix * a.out.ps + a.out.off + co, f);
-            }
-          }
+          for (int j = 0; j < 16; ++j)
+            if (cb + j < a.Cout) st_f(out, pix * a.out.ps + a.out.off + cb + j, f[j]);
         }
       }
     }
@@ -891,7 +920,8 @@ void conv_tc_v(const TcConvArgs& a, cudaStream_t s) {
                          (int)smem);
     attr = true;
   }
-  dim3 grid((unsigned)((long long)a.N * ((a.H + RR - 1) / RR) * ((a.W + 127) / 128)));
+  dim3 grid((unsigned)((long long)a.N * ((a.H + RR - 1) / RR) * ((a.W + 127) / 128)),
+            (unsigned)((a.Cout + NT - 1) / NT));
   k_conv_tc<K, NT, RR, TO><<<grid, 256, smem, s>>>(a);
   count_launches(1);
 }
@@ -918,11 +948,13 @@ bool conv_tc(Tensor in, const bf16* w, const float* bias, Tensor out, int N, int
   a.err = err;
   const int nt = (Cout + 15) / 16 * 16;
   if constexpr (K == 3) {
+    // output rows per CTA: the staged input rows serve RR outputs (TMEM:
+    // RR x NT <= 256); wider outputs are split into NT-channel tiles
     switch (nt) {
-      // output rows per CTA: the staged input rows serve RR outputs (TMEM: RR x NT <= 256)
       case 16: conv_tc_v<3, 16, 4, TO>(a, s); return true;
-      case 48: conv_tc_v<3, 48, 4, TO>(a, s); return true;
-      case 96: conv_tc_v<3, 96, 2, TO>(a, s); return true;
+      case 48: case 144: conv_tc_v<3, 48, 4, TO>(a, s); return true;
+      case 64: conv_tc_v<3, 64, 4, TO>(a, s); return true;
+      case 96: case 288: conv_tc_v<3, 96, 2, TO>(a, s); return true;
       case 192: conv_tc_v<3, 192, 1, TO>(a, s); return true;
       default: return false;
     }
@@ -1070,6 +1102,22 @@ void net_forward(ashrt_unet* u, int n, cudaStream_t s, float* head_planar = null
   count_launches(7);   // pools, upsamplings, first layer
 }
 
+// Input gradient of 3x3 layer l: the output gradient g (masked by the layer's
+// ReLU output act), rounded to BF16, convolved on the tensor cores with the
+// flipped, transposed weights; the CUDA-core kernel (FP32 gradient) where the
+// tcgen05 kernel has no tile for the sizes.
+void bwd_data(ashrt_unet* u, Tensor g, Tensor act, const Layer& l, Tensor out, int n, int H, int W,
+              int Cin, int Cout, cudaStream_t s) {
+  const long long npix = (long long)n * H * W;
+  if (Cin % 16 == 0 && ((g.ps | g.off) & 7) == 0 && ((act.ps | act.off) & 7) == 0) {
+    k_gz_bf16<<<grid1d(npix * Cin / 8), 256, 0, s>>>(g, act, u->gzb, npix, Cin);
+    count_launches(1);
+    if (conv_tc<3, float>(T_(u->gzb, Cin), l.wtn, nullptr, out, n, H, W, Cin, Cout, 0, nullptr, s))
+      return;
+  }
+  conv<3, float, float>(g, act, l.wt, nullptr, out, n, H, W, Cin, Cout, 0, s);
+}
+
 // Backward pass from u->gy (NHWC fp32); accumulates parameter gradients in u->g.
 void net_backward(ashrt_unet* u, int n, cudaStream_t s) {
   const int H = u->H, W = u->W, c0 = u->ch[0], c1 = u->ch[1], c2 = u->ch[2], c3 = u->ch[3];
@@ -1087,43 +1135,43 @@ void net_backward(ashrt_unet* u, int n, cudaStream_t s) {
   conv<1, float, float>(T_(u->gy, u->cout), none, L[14].wt, nullptr, T_(u->gd1b, c0), n, H, W, u->cout, c0, 0, s);
   // dec1
   wgrad<3>(T_(u->d1a, c0), T_(u->gd1b, c0), T_(u->d1b, c0), GW(13), GB(13), n, H, W, c0, c0, s);
-  conv<3, float, float>(T_(u->gd1b, c0), T_(u->d1b, c0), L[13].wt, nullptr, T_(u->gd1a, c0), n, H, W, c0, c0, 0, s);
+  bwd_data(u, T_(u->gd1b, c0), T_(u->d1b, c0), L[13], T_(u->gd1a, c0), n, H, W, c0, c0, s);
   wgrad<3>(T_(u->cat1, c1 + c0), T_(u->gd1a, c0), T_(u->d1a, c0), GW(12), GB(12), n, H, W, c1 + c0, c0, s);
-  conv<3, float, float>(T_(u->gd1a, c0), T_(u->d1a, c0), L[12].wt, nullptr, T_(u->gcat1, c1 + c0), n, H, W, c0, c1 + c0, 0, s);
+  bwd_data(u, T_(u->gd1a, c0), T_(u->d1a, c0), L[12], T_(u->gcat1, c1 + c0), n, H, W, c0, c1 + c0, s);
   k_up_bwd<<<grid((long long)n * H * W / 4 * c1), 256, 0, s>>>(T_(u->gcat1, c1 + c0, 0), T_(u->gd2b, c1), n, H / 2, W / 2, c1);
   // dec2
   wgrad<3>(T_(u->d2a, c1), T_(u->gd2b, c1), T_(u->d2b, c1), GW(11), GB(11), n, H / 2, W / 2, c1, c1, s);
-  conv<3, float, float>(T_(u->gd2b, c1), T_(u->d2b, c1), L[11].wt, nullptr, T_(u->gd2a, c1), n, H / 2, W / 2, c1, c1, 0, s);
+  bwd_data(u, T_(u->gd2b, c1), T_(u->d2b, c1), L[11], T_(u->gd2a, c1), n, H / 2, W / 2, c1, c1, s);
   wgrad<3>(T_(u->cat2, c2 + c1), T_(u->gd2a, c1), T_(u->d2a, c1), GW(10), GB(10), n, H / 2, W / 2, c2 + c1, c1, s);
-  conv<3, float, float>(T_(u->gd2a, c1), T_(u->d2a, c1), L[10].wt, nullptr, T_(u->gcat2, c2 + c1), n, H / 2, W / 2, c1, c2 + c1, 0, s);
+  bwd_data(u, T_(u->gd2a, c1), T_(u->d2a, c1), L[10], T_(u->gcat2, c2 + c1), n, H / 2, W / 2, c1, c2 + c1, s);
   k_up_bwd<<<grid((long long)n * H * W / 16 * c2), 256, 0, s>>>(T_(u->gcat2, c2 + c1, 0), T_(u->gd3b, c2), n, H / 4, W / 4, c2);
   // dec3
   wgrad<3>(T_(u->d3a, c2), T_(u->gd3b, c2), T_(u->d3b, c2), GW(9), GB(9), n, H / 4, W / 4, c2, c2, s);
-  conv<3, float, float>(T_(u->gd3b, c2), T_(u->d3b, c2), L[9].wt, nullptr, T_(u->gd3a, c2), n, H / 4, W / 4, c2, c2, 0, s);
+  bwd_data(u, T_(u->gd3b, c2), T_(u->d3b, c2), L[9], T_(u->gd3a, c2), n, H / 4, W / 4, c2, c2, s);
   wgrad<3>(T_(u->cat3, c3 + c2), T_(u->gd3a, c2), T_(u->d3a, c2), GW(8), GB(8), n, H / 4, W / 4, c3 + c2, c2, s);
-  conv<3, float, float>(T_(u->gd3a, c2), T_(u->d3a, c2), L[8].wt, nullptr, T_(u->gcat3, c3 + c2), n, H / 4, W / 4, c2, c3 + c2, 0, s);
+  bwd_data(u, T_(u->gd3a, c2), T_(u->d3a, c2), L[8], T_(u->gcat3, c3 + c2), n, H / 4, W / 4, c2, c3 + c2, s);
   k_up_bwd<<<grid((long long)n * H * W / 64 * c3), 256, 0, s>>>(T_(u->gcat3, c3 + c2, 0), T_(u->gbb, c3), n, H / 8, W / 8, c3);
   // bottleneck
   wgrad<3>(T_(u->ba, c3), T_(u->gbb, c3), T_(u->bb, c3), GW(7), GB(7), n, H / 8, W / 8, c3, c3, s);
-  conv<3, float, float>(T_(u->gbb, c3), T_(u->bb, c3), L[7].wt, nullptr, T_(u->gba, c3), n, H / 8, W / 8, c3, c3, 0, s);
+  bwd_data(u, T_(u->gbb, c3), T_(u->bb, c3), L[7], T_(u->gba, c3), n, H / 8, W / 8, c3, c3, s);
   wgrad<3>(T_(u->p3, c2), T_(u->gba, c3), T_(u->ba, c3), GW(6), GB(6), n, H / 8, W / 8, c2, c3, s);
-  conv<3, float, float>(T_(u->gba, c3), T_(u->ba, c3), L[6].wt, nullptr, T_(u->gp3, c2), n, H / 8, W / 8, c3, c2, 0, s);
+  bwd_data(u, T_(u->gba, c3), T_(u->ba, c3), L[6], T_(u->gp3, c2), n, H / 8, W / 8, c3, c2, s);
   k_pool_bwd_acc<<<grid((long long)n * H * W / 16 * c2), 256, 0, s>>>(T_(u->gp3, c2), T_(u->gcat3, c3 + c2, c3), n, H / 4, W / 4, c2);
   // enc3 (its output s3 lives in cat3[c3:], gradient in gcat3[c3:])
   wgrad<3>(T_(u->e3a, c2), T_(u->gcat3, c3 + c2, c3), T_(u->cat3, c3 + c2, c3), GW(5), GB(5), n, H / 4, W / 4, c2, c2, s);
-  conv<3, float, float>(T_(u->gcat3, c3 + c2, c3), T_(u->cat3, c3 + c2, c3), L[5].wt, nullptr, T_(u->g3a, c2), n, H / 4, W / 4, c2, c2, 0, s);
+  bwd_data(u, T_(u->gcat3, c3 + c2, c3), T_(u->cat3, c3 + c2, c3), L[5], T_(u->g3a, c2), n, H / 4, W / 4, c2, c2, s);
   wgrad<3>(T_(u->p2, c1), T_(u->g3a, c2), T_(u->e3a, c2), GW(4), GB(4), n, H / 4, W / 4, c1, c2, s);
-  conv<3, float, float>(T_(u->g3a, c2), T_(u->e3a, c2), L[4].wt, nullptr, T_(u->gp2, c1), n, H / 4, W / 4, c2, c1, 0, s);
+  bwd_data(u, T_(u->g3a, c2), T_(u->e3a, c2), L[4], T_(u->gp2, c1), n, H / 4, W / 4, c2, c1, s);
   k_pool_bwd_acc<<<grid((long long)n * H * W / 4 * c1), 256, 0, s>>>(T_(u->gp2, c1), T_(u->gcat2, c2 + c1, c2), n, H / 2, W / 2, c1);
   // enc2
   wgrad<3>(T_(u->e2a, c1), T_(u->gcat2, c2 + c1, c2), T_(u->cat2, c2 + c1, c2), GW(3), GB(3), n, H / 2, W / 2, c1, c1, s);
-  conv<3, float, float>(T_(u->gcat2, c2 + c1, c2), T_(u->cat2, c2 + c1, c2), L[3].wt, nullptr, T_(u->g2a, c1), n, H / 2, W / 2, c1, c1, 0, s);
+  bwd_data(u, T_(u->gcat2, c2 + c1, c2), T_(u->cat2, c2 + c1, c2), L[3], T_(u->g2a, c1), n, H / 2, W / 2, c1, c1, s);
   wgrad<3>(T_(u->p1, c0), T_(u->g2a, c1), T_(u->e2a, c1), GW(2), GB(2), n, H / 2, W / 2, c0, c1, s);
-  conv<3, float, float>(T_(u->g2a, c1), T_(u->e2a, c1), L[2].wt, nullptr, T_(u->gp1, c0), n, H / 2, W / 2, c1, c0, 0, s);
+  bwd_data(u, T_(u->g2a, c1), T_(u->e2a, c1), L[2], T_(u->gp1, c0), n, H / 2, W / 2, c1, c0, s);
   k_pool_bwd_acc<<<grid((long long)n * H * W * c0), 256, 0, s>>>(T_(u->gp1, c0), T_(u->gcat1, c1 + c0, c1), n, H, W, c0);
   // enc1
   wgrad<3>(T_(u->e1a, c0), T_(u->gcat1, c1 + c0, c1), T_(u->cat1, c1 + c0, c1), GW(1), GB(1), n, H, W, c0, c0, s);
-  conv<3, float, float>(T_(u->gcat1, c1 + c0, c1), T_(u->cat1, c1 + c0, c1), L[1].wt, nullptr, T_(u->g1a, c0), n, H, W, c0, c0, 0, s);
+  bwd_data(u, T_(u->gcat1, c1 + c0, c1), T_(u->cat1, c1 + c0, c1), L[1], T_(u->g1a, c0), n, H, W, c0, c0, s);
   wgrad<3>(T_(u->x, 1), T_(u->g1a, c0), T_(u->e1a, c0), GW(0), GB(0), n, H, W, 1, c0, s);
   count_launches(6);
 }
@@ -1131,7 +1179,8 @@ void net_backward(ashrt_unet* u, int n, cudaStream_t s) {
 cudaError_t refresh_bf16_weights(ashrt_unet* u, cudaStream_t s) {
   for (auto& l : u->L) {
     const int total = l.co * l.ci * l.k * l.k;
-    k_wconv<<<(total + 255) / 256, 256, 0, s>>>(u->w + l.w_off, l.wf, l.wt, l.wn, l.co, l.ci, l.k);
+    k_wconv<<<(total + 255) / 256, 256, 0, s>>>(u->w + l.w_off, l.wf, l.wt, l.wn, l.wtn, l.co,
+                                                l.ci, l.k);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -1184,6 +1233,7 @@ ashrt_status ashrt_unet_create(ashrt_unet** out, int H, int W, int out_channels,
     A(&l.wf, (size_t)l.co * l.ci * l.k * l.k);
     A(&l.wt, (size_t)l.co * l.ci * l.k * l.k);
     A(&l.wn, (size_t)l.co * l.ci * l.k * l.k);
+    A(&l.wtn, (size_t)l.co * l.ci * l.k * l.k);
   }
   A(&u->x, P0);
   A(&u->e1a, P0 * c0);
@@ -1224,6 +1274,7 @@ ashrt_status ashrt_unet_create(ashrt_unet** out, int H, int W, int out_channels,
   A(&u->gd1b, P0 * c0);
   A(&u->rms, max_batch);
   A(&u->rmsacc, max_batch);
+  A(&u->gzb, P0 * c0);
   A(&u->lam, out_channels);
   A(&u->loss, 1);
   if (e != cudaSuccess) {

@@ -99,3 +99,24 @@ def test_rounded_network_reduces_to_exact_on_representable_values():
     y2, _ = unet.forward(p, x, 3, ch, rnd=unet.bf16_round)
     rel = np.linalg.norm(y2 - y0) / np.linalg.norm(y0)
     assert 1e-5 < rel < 3e-2
+
+
+def test_gradient_rounding_hook_only_touches_input_gradients():
+    """rnd_g = identity reproduces the exact backward; a real rounding leaves
+    the head's and every weight gradient of the last layer it reaches first
+    (dec1b) unchanged and perturbs the earlier layers only slightly."""
+    rng = np.random.default_rng(7)
+    ch = (4, 6, 8, 10)
+    p = unet.init_params(rng, 1, 3, ch)
+    x = rng.standard_normal((1, 1, 16, 16))
+    y, cache = unet.forward(p, x, 3, ch)
+    gy = rng.standard_normal(y.shape)
+    g0 = unet.backward(p, cache, gy, ch)
+    g1 = unet.backward(p, cache, gy, ch, rnd_g=lambda v: v)
+    for k in g0:
+        np.testing.assert_array_equal(g0[k], g1[k])
+    g2 = unet.backward(p, cache, gy, ch, rnd_g=unet.bf16_round)
+    for k in ("head.w", "head.b", "dec1b.w", "dec1b.b"):
+        np.testing.assert_array_equal(g0[k], g2[k])
+    rel = np.linalg.norm(g2["enc1a.w"] - g0["enc1a.w"]) / np.linalg.norm(g0["enc1a.w"])
+    assert 0.0 < rel < 3e-2
