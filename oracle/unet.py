@@ -134,21 +134,19 @@ def backward(p, cache, gy, ch=CHANNELS, rnd=None, rnd_g=None):
     """Gradients of sum(gy * y) with respect to every parameter.
 
     rnd: the rounding of the weights used in the forward pass.  rnd_g
-    (optional): a rounding of the masked output gradient of each 3x3 layer
-    before it is propagated to the layer's input (the weight and bias
-    gradients use the unrounded one; the head's input gradient is not
-    rounded), which models a network that runs that propagation at reduced
-    precision.  None = exact."""
+    (optional): a rounding of the masked output gradient of each 3x3 layer,
+    used for that layer's input, weight and bias gradients (the head's
+    gradient is not rounded), which models a network that runs those
+    products at reduced precision.  None = exact."""
     c0, c1, c2, c3 = ch
     g = {}
     q = (lambda v: v) if rnd is None else rnd
+    qg = (lambda v: v) if rnd_g is None else rnd_g
 
     def cr_back(name, ga):
         inp, a = cache[name]
-        gz = ga * (a > 0.0)
+        gz = qg(ga * (a > 0.0))
         gx, gw, gb = conv_backward(inp, q(p[name + ".w"]), gz)
-        if rnd_g is not None:
-            gx = conv_backward(inp, q(p[name + ".w"]), rnd_g(gz))[0]
         g[name + ".w"], g[name + ".b"] = gw, gb
         return gx
 

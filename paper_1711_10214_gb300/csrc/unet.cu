@@ -1102,20 +1102,169 @@ void net_forward(ashrt_unet* u, int n, cudaStream_t s, float* head_planar = null
   count_launches(7);   // pools, upsamplings, first layer
 }
 
-// Input gradient of 3x3 layer l: the output gradient g (masked by the layer's
-// ReLU output act), rounded to BF16, convolved on the tensor cores with the
-// flipped, transposed weights; the CUDA-core kernel (FP32 gradient) where the
-// tcgen05 kernel has no tile for the sizes.
-void bwd_data(ashrt_unet* u, Tensor g, Tensor act, const Layer& l, Tensor out, int n, int H, int W,
-              int Cin, int Cout, cudaStream_t s) {
-  const long long npix = (long long)n * H * W;
-  if (Cin % 16 == 0 && ((g.ps | g.off) & 7) == 0 && ((act.ps | act.off) & 7) == 0) {
-    k_gz_bf16<<<grid1d(npix * Cin / 8), 256, 0, s>>>(g, act, u->gzb, npix, Cin);
-    count_launches(1);
-    if (conv_tc<3, float>(T_(u->gzb, Cin), l.wtn, nullptr, out, n, H, W, Cin, Cout, 0, nullptr, s))
-      return;
+// Weight and bias gradients of a 3x3 layer on the tensor cores (mma.sync
+// m16n8k16, BF16 operands, FP32 accumulation): for every tap, an implicit GEMM
+// gw[co][ci] += sum_p gz[p][co] x[p + tap][ci] over the pixels p, M = output
+// channels, N = input channels, K = pixels.  A CTA owns 16 MT output x 32 input
+// channels and all nine taps and reduces a 128-pixel column strip of rows_per
+// image rows: per row it stages the BF16 masked output gradient [128][16 MT]
+// and the three input rows [3][130][32] in their NHWC order and reads both
+// operands with ldmatrix.trans; the FP32 partial sums leave with one atomic
+// each.  CTAs of the first input-channel tile also sum the bias gradient.
+struct WgMmaArgs {
+  Tensor in;            // bf16 layer input slice (ps, off multiples of 8)
+  const bf16* gz;       // bf16 masked output gradient, dense [pixels][Cout]
+  float* gw;            // [Cout][Cin][3][3] fp32, accumulated
+  float* gb;            // [Cout] fp32, accumulated
+  int N, H, W, Cin, Cout, rows_per;
+};
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
+                                          const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+}
+
+__device__ __forceinline__ void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];\n"
+               : "=r"(r0), "=r"(r1)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+}
+
+template <int MT>
+__global__ void __launch_bounds__(256) k_wgrad_mma(WgMmaArgs a) {
+  constexpr int CO_T = 16 * MT, CI_T = 32, LDX = CI_T + 8, LDG = CO_T + 8, PW = 130;
+  constexpr int TILES = 9 * MT * 4, PER = (TILES + 7) / 8;
+  __shared__ __align__(16) bf16 xs[3 * PW * LDX];
+  __shared__ __align__(16) bf16 gs[128 * LDG];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int xt = (a.W + 127) / 128;
+  const int x0 = (blockIdx.x % xt) * 128;
+  const int row0 = (blockIdx.x / xt) * a.rows_per;
+  const int row1 = min(row0 + a.rows_per, a.N * a.H);
+  const int ci0 = blockIdx.y * CI_T, co0 = blockIdx.z * CO_T;
+  const bf16* in = (const bf16*)a.in.p;
+  float acc[PER][4];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  float bsum = 0.f;
+
+  for (int row = row0; row < row1; ++row) {
+    const int n = row / a.H, y = row % a.H;
+    for (int e = tid; e < 3 * PW * 4; e += 256) {
+      const int q = e % 4, px = (e / 4) % PW, r = e / (4 * PW);
+      const int yy = y + r - 1, xx = x0 + px - 1, c = ci0 + 8 * q;
+      const bool ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && c < a.Cin;
+      const bf16* src = ok ? in + (((long long)n * a.H + yy) * a.W + xx) * a.in.ps + a.in.off + c : in;
+      cp16(xs + (r * PW + px) * LDX + 8 * q, src, ok);
+    }
+    for (int e = tid; e < 128 * (CO_T / 8); e += 256) {
+      const int q = e % (CO_T / 8), px = e / (CO_T / 8);
+      const int xx = x0 + px, c = co0 + 8 * q;
+      const bool ok = xx < a.W && c < a.Cout;
+      const bf16* src = ok ? a.gz + (((long long)n * a.H + y) * a.W + xx) * a.Cout + c : a.gz;
+      cp16(gs + px * LDG + 8 * q, src, ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    if (blockIdx.y == 0 && tid < CO_T)
+      for (int px = 0; px < 128; ++px) bsum += __bfloat162float(gs[px * LDG + tid]);
+#pragma unroll 2
+    for (int kb = 0; kb < 128; kb += 16) {
+      uint32_t af[MT][4];
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int kr = kb + (lane & 7) + ((lane >> 4) << 3), mc = mt * 16 + (((lane >> 3) & 1) << 3);
+        ldsm_x4_t(af[mt][0], af[mt][1], af[mt][2], af[mt][3], gs + kr * LDG + mc);
+      }
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int id = warp + 8 * j;
+        if (id < TILES) {
+          const int tap = id / (4 * MT), mt = (id / 4) % MT, nt = id % 4;
+          const int dy = tap / 3, dx = tap % 3;
+          const int kr = kb + dx + (lane & 7) + (((lane >> 3) & 1) << 3);
+          uint32_t b0, b1;
+          ldsm_x2_t(b0, b1, xs + (dy * PW + kr) * LDX + nt * 8);
+          // select the A fragment with conditionals (a register array indexed
+          // by a runtime value would live in local memory)
+          const bool m1 = MT > 1 && mt == 1;
+          mma_bf16(acc[j], m1 ? af[MT - 1][0] : af[0][0], m1 ? af[MT - 1][1] : af[0][1],
+                   m1 ? af[MT - 1][2] : af[0][2], m1 ? af[MT - 1][3] : af[0][3], b0, b1);
+        }
+      }
+    }
+    __syncthreads();
   }
-  conv<3, float, float>(g, act, l.wt, nullptr, out, n, H, W, Cin, Cout, 0, s);
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int id = warp + 8 * j;
+    if (id >= TILES) continue;
+    const int tap = id / (4 * MT), mt = (id / 4) % MT, nt = id % 4;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int co = co0 + mt * 16 + g + 8 * h;
+      if (co >= a.Cout) continue;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int ci = ci0 + nt * 8 + 2 * t + u;
+        if (ci < a.Cin) atomicAdd(&a.gw[((long long)co * a.Cin + ci) * 9 + tap], acc[j][2 * h + u]);
+      }
+    }
+  }
+  if (blockIdx.y == 0 && tid < CO_T && co0 + tid < a.Cout) atomicAdd(&a.gb[co0 + tid], bsum);
+}
+
+template <int MT>
+void wgrad_mma_v(const WgMmaArgs& a0, cudaStream_t s) {
+  WgMmaArgs a = a0;
+  const int xt = (a.W + 127) / 128;
+  const long long ch_tiles = (long long)((a.Cin + 31) / 32) * ((a.Cout + 16 * MT - 1) / (16 * MT));
+  const long long want = (152LL * 8 + ch_tiles - 1) / ch_tiles;
+  const long long rows = (long long)a.N * a.H;
+  long long per_col = (want + xt - 1) / xt;
+  per_col = std::max(1LL, std::min(per_col, rows));
+  a.rows_per = (int)((rows + per_col - 1) / per_col);
+  const long long nstrip = (rows + a.rows_per - 1) / a.rows_per;
+  dim3 grid((unsigned)(nstrip * xt), (a.Cin + 31) / 32, (a.Cout + 16 * MT - 1) / (16 * MT));
+  k_wgrad_mma<MT><<<grid, 256, 0, s>>>(a);
+  count_launches(1);
+}
+
+// Backward of 3x3 layer l (input `in`, output gradient g masked by its ReLU
+// output act): weight and bias gradients and, if out.p, the input gradient.
+// On the tensor cores the masked gradient is rounded to BF16 once and serves
+// both products; otherwise the CUDA-core kernels work on the FP32 gradient.
+void layer_backward(ashrt_unet* u, Tensor in, Tensor g, Tensor act, const Layer& l, float* gw,
+                    float* gb, Tensor out, int n, int H, int W, int Cin, int Cout, cudaStream_t s) {
+  const long long npix = (long long)n * H * W;
+  const bool tc = Cin % 16 == 0 && Cout % 16 == 0 && ((in.ps | in.off) & 7) == 0 &&
+                  ((g.ps | g.off) & 7) == 0 && ((act.ps | act.off) & 7) == 0;
+  if (!tc) {
+    wgrad<3>(in, g, act, gw, gb, n, H, W, Cin, Cout, s);
+    if (out.p) conv<3, float, float>(g, act, l.wt, nullptr, out, n, H, W, Cout, Cin, 0, s);
+    return;
+  }
+  k_gz_bf16<<<grid1d(npix * Cout / 8), 256, 0, s>>>(g, act, u->gzb, npix, Cout);
+  count_launches(1);
+  WgMmaArgs a;
+  a.in = in;
+  a.gz = u->gzb;
+  a.gw = gw;
+  a.gb = gb;
+  a.N = n;
+  a.H = H;
+  a.W = W;
+  a.Cin = Cin;
+  a.Cout = Cout;
+  if (Cout <= 16) wgrad_mma_v<1>(a, s);
+  else wgrad_mma_v<2>(a, s);
+  if (out.p && !conv_tc<3, float>(T_(u->gzb, Cout), l.wtn, nullptr, out, n, H, W, Cout, Cin, 0,
+                                  nullptr, s))
+    conv<3, float, float>(g, act, l.wt, nullptr, out, n, H, W, Cout, Cin, 0, s);
 }
 
 // Backward pass from u->gy (NHWC fp32); accumulates parameter gradients in u->g.
@@ -1134,45 +1283,32 @@ void net_backward(ashrt_unet* u, int n, cudaStream_t s) {
   wgrad<1>(T_(u->d1b, c0), T_(u->gy, u->cout), none, GW(14), GB(14), n, H, W, c0, u->cout, s);
   conv<1, float, float>(T_(u->gy, u->cout), none, L[14].wt, nullptr, T_(u->gd1b, c0), n, H, W, u->cout, c0, 0, s);
   // dec1
-  wgrad<3>(T_(u->d1a, c0), T_(u->gd1b, c0), T_(u->d1b, c0), GW(13), GB(13), n, H, W, c0, c0, s);
-  bwd_data(u, T_(u->gd1b, c0), T_(u->d1b, c0), L[13], T_(u->gd1a, c0), n, H, W, c0, c0, s);
-  wgrad<3>(T_(u->cat1, c1 + c0), T_(u->gd1a, c0), T_(u->d1a, c0), GW(12), GB(12), n, H, W, c1 + c0, c0, s);
-  bwd_data(u, T_(u->gd1a, c0), T_(u->d1a, c0), L[12], T_(u->gcat1, c1 + c0), n, H, W, c0, c1 + c0, s);
+  layer_backward(u, T_(u->d1a, c0), T_(u->gd1b, c0), T_(u->d1b, c0), L[13], GW(13), GB(13), T_(u->gd1a, c0), n, H, W, c0, c0, s);
+  layer_backward(u, T_(u->cat1, c1 + c0), T_(u->gd1a, c0), T_(u->d1a, c0), L[12], GW(12), GB(12), T_(u->gcat1, c1 + c0), n, H, W, c1 + c0, c0, s);
   k_up_bwd<<<grid((long long)n * H * W / 4 * c1), 256, 0, s>>>(T_(u->gcat1, c1 + c0, 0), T_(u->gd2b, c1), n, H / 2, W / 2, c1);
   // dec2
-  wgrad<3>(T_(u->d2a, c1), T_(u->gd2b, c1), T_(u->d2b, c1), GW(11), GB(11), n, H / 2, W / 2, c1, c1, s);
-  bwd_data(u, T_(u->gd2b, c1), T_(u->d2b, c1), L[11], T_(u->gd2a, c1), n, H / 2, W / 2, c1, c1, s);
-  wgrad<3>(T_(u->cat2, c2 + c1), T_(u->gd2a, c1), T_(u->d2a, c1), GW(10), GB(10), n, H / 2, W / 2, c2 + c1, c1, s);
-  bwd_data(u, T_(u->gd2a, c1), T_(u->d2a, c1), L[10], T_(u->gcat2, c2 + c1), n, H / 2, W / 2, c1, c2 + c1, s);
+  layer_backward(u, T_(u->d2a, c1), T_(u->gd2b, c1), T_(u->d2b, c1), L[11], GW(11), GB(11), T_(u->gd2a, c1), n, H / 2, W / 2, c1, c1, s);
+  layer_backward(u, T_(u->cat2, c2 + c1), T_(u->gd2a, c1), T_(u->d2a, c1), L[10], GW(10), GB(10), T_(u->gcat2, c2 + c1), n, H / 2, W / 2, c2 + c1, c1, s);
   k_up_bwd<<<grid((long long)n * H * W / 16 * c2), 256, 0, s>>>(T_(u->gcat2, c2 + c1, 0), T_(u->gd3b, c2), n, H / 4, W / 4, c2);
   // dec3
-  wgrad<3>(T_(u->d3a, c2), T_(u->gd3b, c2), T_(u->d3b, c2), GW(9), GB(9), n, H / 4, W / 4, c2, c2, s);
-  bwd_data(u, T_(u->gd3b, c2), T_(u->d3b, c2), L[9], T_(u->gd3a, c2), n, H / 4, W / 4, c2, c2, s);
-  wgrad<3>(T_(u->cat3, c3 + c2), T_(u->gd3a, c2), T_(u->d3a, c2), GW(8), GB(8), n, H / 4, W / 4, c3 + c2, c2, s);
-  bwd_data(u, T_(u->gd3a, c2), T_(u->d3a, c2), L[8], T_(u->gcat3, c3 + c2), n, H / 4, W / 4, c2, c3 + c2, s);
+  layer_backward(u, T_(u->d3a, c2), T_(u->gd3b, c2), T_(u->d3b, c2), L[9], GW(9), GB(9), T_(u->gd3a, c2), n, H / 4, W / 4, c2, c2, s);
+  layer_backward(u, T_(u->cat3, c3 + c2), T_(u->gd3a, c2), T_(u->d3a, c2), L[8], GW(8), GB(8), T_(u->gcat3, c3 + c2), n, H / 4, W / 4, c3 + c2, c2, s);
   k_up_bwd<<<grid((long long)n * H * W / 64 * c3), 256, 0, s>>>(T_(u->gcat3, c3 + c2, 0), T_(u->gbb, c3), n, H / 8, W / 8, c3);
   // bottleneck
-  wgrad<3>(T_(u->ba, c3), T_(u->gbb, c3), T_(u->bb, c3), GW(7), GB(7), n, H / 8, W / 8, c3, c3, s);
-  bwd_data(u, T_(u->gbb, c3), T_(u->bb, c3), L[7], T_(u->gba, c3), n, H / 8, W / 8, c3, c3, s);
-  wgrad<3>(T_(u->p3, c2), T_(u->gba, c3), T_(u->ba, c3), GW(6), GB(6), n, H / 8, W / 8, c2, c3, s);
-  bwd_data(u, T_(u->gba, c3), T_(u->ba, c3), L[6], T_(u->gp3, c2), n, H / 8, W / 8, c3, c2, s);
+  layer_backward(u, T_(u->ba, c3), T_(u->gbb, c3), T_(u->bb, c3), L[7], GW(7), GB(7), T_(u->gba, c3), n, H / 8, W / 8, c3, c3, s);
+  layer_backward(u, T_(u->p3, c2), T_(u->gba, c3), T_(u->ba, c3), L[6], GW(6), GB(6), T_(u->gp3, c2), n, H / 8, W / 8, c2, c3, s);
   k_pool_bwd_acc<<<grid((long long)n * H * W / 16 * c2), 256, 0, s>>>(T_(u->gp3, c2), T_(u->gcat3, c3 + c2, c3), n, H / 4, W / 4, c2);
   // enc3 (its output s3 lives in cat3[c3:], gradient in gcat3[c3:])
-  wgrad<3>(T_(u->e3a, c2), T_(u->gcat3, c3 + c2, c3), T_(u->cat3, c3 + c2, c3), GW(5), GB(5), n, H / 4, W / 4, c2, c2, s);
-  bwd_data(u, T_(u->gcat3, c3 + c2, c3), T_(u->cat3, c3 + c2, c3), L[5], T_(u->g3a, c2), n, H / 4, W / 4, c2, c2, s);
-  wgrad<3>(T_(u->p2, c1), T_(u->g3a, c2), T_(u->e3a, c2), GW(4), GB(4), n, H / 4, W / 4, c1, c2, s);
-  bwd_data(u, T_(u->g3a, c2), T_(u->e3a, c2), L[4], T_(u->gp2, c1), n, H / 4, W / 4, c2, c1, s);
+  layer_backward(u, T_(u->e3a, c2), T_(u->gcat3, c3 + c2, c3), T_(u->cat3, c3 + c2, c3), L[5], GW(5), GB(5), T_(u->g3a, c2), n, H / 4, W / 4, c2, c2, s);
+  layer_backward(u, T_(u->p2, c1), T_(u->g3a, c2), T_(u->e3a, c2), L[4], GW(4), GB(4), T_(u->gp2, c1), n, H / 4, W / 4, c1, c2, s);
   k_pool_bwd_acc<<<grid((long long)n * H * W / 4 * c1), 256, 0, s>>>(T_(u->gp2, c1), T_(u->gcat2, c2 + c1, c2), n, H / 2, W / 2, c1);
   // enc2
-  wgrad<3>(T_(u->e2a, c1), T_(u->gcat2, c2 + c1, c2), T_(u->cat2, c2 + c1, c2), GW(3), GB(3), n, H / 2, W / 2, c1, c1, s);
-  bwd_data(u, T_(u->gcat2, c2 + c1, c2), T_(u->cat2, c2 + c1, c2), L[3], T_(u->g2a, c1), n, H / 2, W / 2, c1, c1, s);
-  wgrad<3>(T_(u->p1, c0), T_(u->g2a, c1), T_(u->e2a, c1), GW(2), GB(2), n, H / 2, W / 2, c0, c1, s);
-  bwd_data(u, T_(u->g2a, c1), T_(u->e2a, c1), L[2], T_(u->gp1, c0), n, H / 2, W / 2, c1, c0, s);
+  layer_backward(u, T_(u->e2a, c1), T_(u->gcat2, c2 + c1, c2), T_(u->cat2, c2 + c1, c2), L[3], GW(3), GB(3), T_(u->g2a, c1), n, H / 2, W / 2, c1, c1, s);
+  layer_backward(u, T_(u->p1, c0), T_(u->g2a, c1), T_(u->e2a, c1), L[2], GW(2), GB(2), T_(u->gp1, c0), n, H / 2, W / 2, c0, c1, s);
   k_pool_bwd_acc<<<grid((long long)n * H * W * c0), 256, 0, s>>>(T_(u->gp1, c0), T_(u->gcat1, c1 + c0, c1), n, H, W, c0);
   // enc1
-  wgrad<3>(T_(u->e1a, c0), T_(u->gcat1, c1 + c0, c1), T_(u->cat1, c1 + c0, c1), GW(1), GB(1), n, H, W, c0, c0, s);
-  bwd_data(u, T_(u->gcat1, c1 + c0, c1), T_(u->cat1, c1 + c0, c1), L[1], T_(u->g1a, c0), n, H, W, c0, c0, s);
-  wgrad<3>(T_(u->x, 1), T_(u->g1a, c0), T_(u->e1a, c0), GW(0), GB(0), n, H, W, 1, c0, s);
+  layer_backward(u, T_(u->e1a, c0), T_(u->gcat1, c1 + c0, c1), T_(u->cat1, c1 + c0, c1), L[1], GW(1), GB(1), T_(u->g1a, c0), n, H, W, c0, c0, s);
+  layer_backward(u, T_(u->x, 1), T_(u->g1a, c0), T_(u->e1a, c0), L[0], GW(0), GB(0), none, n, H, W, 1, c0, s);
   count_launches(6);
 }
 

@@ -3,10 +3,9 @@ reference network of ``oracle/unet.py``.
 
 Two references.  (1) The FP64 network with the storage rounding modelled
 (weights, input and stored activations rounded to bfloat16, and the masked
-output gradient of each 3x3 layer rounded to bfloat16 before it is propagated
-to the layer's input, as the tensor-core input-gradient convolution takes it;
-everything else exact): the kernels differ from it only by FP32 accumulation
-order and the
+output gradient of each 3x3 layer rounded to bfloat16, as the tensor-core
+input- and weight-gradient kernels take it; everything else exact): the
+kernels differ from it only by FP32 accumulation order and the
 activations that this order pushes to the neighbouring bfloat16 value (one
 bfloat16 step is 2^-8 relative; after cancellation in a 9 Cin-term sum the FP32
 result can be off by ~1e-5 relative, so a few in a thousand activations land
