@@ -249,6 +249,9 @@ def main(argv=None):
     ap.add_argument("--processes", type=int, default=min(12, os.cpu_count() or 1))
     ap.add_argument("--out", default=None)
     ap.add_argument("--save-params", default=None)
+    ap.add_argument("--budgets", default=None,
+                    help="evaluation ladder as outer x CG pairs, e.g. 1x5,8x30 "
+                         "(default: the full ladder; it must contain 8x30)")
     a = ap.parse_args(argv)
     import multiprocessing as mp
     mp.get_context("spawn")
@@ -260,7 +263,12 @@ def main(argv=None):
     tr = train(ws, a.train, processes=a.processes, passes=a.passes, lr0=a.lr, log=log,
                epochs=a.epochs)
     tr["wall_s"] = time.perf_counter() - t0
-    ev = evaluate(ws, a.test, processes=a.processes)
+    budgets = BUDGETS
+    if a.budgets:
+        budgets = [tuple(int(v) for v in b.split("x")) for b in a.budgets.split(",")]
+        if REFERENCE not in budgets:
+            raise SystemExit("--budgets must contain the reference budget 8x30")
+    ev = evaluate(ws, a.test, processes=a.processes, budgets=budgets)
     res = dict(config=dict(workload="%s warm start" % src.name, nt=src.nt, nx=src.nx,
                            nv=len(src.velocities), params=ws.net.n_params), train=tr, eval=ev)
     print(json.dumps({k: v for k, v in ev.items() if k.endswith("reach") or k.startswith("q_")}))
