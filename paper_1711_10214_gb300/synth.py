@@ -161,7 +161,8 @@ def config5_gather(g, nt=1024, nx=256):
 
 def _c5_job(args):
     g, nt, nx = args
-    return config5_gather(g, nt, nx)
+    c, b = config5_gather(g, nt, nx)
+    return c.astype(np.float32), b.astype(np.float32)
 
 
 def _c1_job(args):

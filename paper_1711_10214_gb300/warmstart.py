@@ -180,7 +180,7 @@ def train(ws, n_train, processes=8, passes=2, lr0=1e-3, lr1=1e-4, log=None, epoc
 
 
 def evaluate(ws, n_test, processes=8, budgets=BUDGETS, margin_db=0.1,
-             arms=("cold", "warm_w", "warm_mw")):
+             arms=("cold", "warm_w", "warm_mw"), warm_budgets=None):
     """Cold and warm solves of gathers TEST_SEED0.. (disjoint from training)
     over the budget ladder.  Arms: cold; warm_w (predicted W_r0, m = 0);
     warm_mw (predicted m0 and W_r0).
@@ -190,7 +190,8 @@ def evaluate(ws, n_test, processes=8, budgets=BUDGETS, margin_db=0.1,
     adjoint, including the warm start's residual apply), and gathers/s (device
     time of prediction + solve).  The target is the cold reference budget's
     mean Q minus margin_db; each arm's answer is its cheapest budget that
-    reaches it.
+    reaches it.  warm_budgets (optional) is a shorter ladder for the warm
+    arms.
     """
     import multiprocessing as mp
     src = ws.source
@@ -206,7 +207,8 @@ def evaluate(ws, n_test, processes=8, budgets=BUDGETS, margin_db=0.1,
     torch = ws.torch
     out = {arm: [] for arm in arms}
     for arm in arms:
-        for (no, nc) in budgets:
+        ladder = budgets if (arm == "cold" or warm_budgets is None) else warm_budgets
+        for (no, nc) in ladder:
             qs, applies, secs = [], 0, 0.0
             for s in range(0, n_test, ws.chunk):
                 n = ws.upload(blended[s:s + ws.chunk])
@@ -249,6 +251,9 @@ def main(argv=None):
     ap.add_argument("--processes", type=int, default=min(12, os.cpu_count() or 1))
     ap.add_argument("--out", default=None)
     ap.add_argument("--save-params", default=None)
+    ap.add_argument("--warm-budgets", default=None,
+                    help="ladder of the warm arms (default: --budgets)")
+    ap.add_argument("--arms", default="cold,warm_w,warm_mw")
     ap.add_argument("--budgets", default=None,
                     help="evaluation ladder as outer x CG pairs, e.g. 1x5,8x30 "
                          "(default: the full ladder; it must contain 8x30)")
@@ -268,7 +273,10 @@ def main(argv=None):
         budgets = [tuple(int(v) for v in b.split("x")) for b in a.budgets.split(",")]
         if REFERENCE not in budgets:
             raise SystemExit("--budgets must contain the reference budget 8x30")
-    ev = evaluate(ws, a.test, processes=a.processes, budgets=budgets)
+    parse = lambda txt: [tuple(int(v) for v in b.split("x")) for b in txt.split(",")]
+    ev = evaluate(ws, a.test, processes=a.processes, budgets=budgets,
+                  arms=tuple(a.arms.split(",")),
+                  warm_budgets=parse(a.warm_budgets) if a.warm_budgets else None)
     res = dict(config=dict(workload="%s warm start" % src.name, nt=src.nt, nx=src.nx,
                            nv=len(src.velocities), params=ws.net.n_params), train=tr, eval=ev)
     print(json.dumps({k: v for k, v in ev.items() if k.endswith("reach") or k.startswith("q_")}))
