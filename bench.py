@@ -140,6 +140,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def whole_job_rate(t_local, units_per_rank, world, dist=None, device=None):
+    """Slowest rank's time and the whole job's rate: every rank processed
+    units_per_rank units in its own t_local seconds; the job took the max over
+    ranks (one all-reduce when distributed)."""
+    t = float(t_local)
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, world * units_per_rank / t
+
+
 def cpu_baseline_sample():
     """The FP64 oracle (numpy, naive DFTs) on one gather of the workload: one
     forward + one adjoint with all 32 velocities, timed on the host cores."""
@@ -243,12 +256,8 @@ def run_ours(args):
     ashrt.profile_enable(False)
     prof = ashrt.profile_read()
     clk = clocks.stop()
-    t = e0.elapsed_time(e1) / 1000.0
-    if dist is not None:
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * pairs_per_step * args.steps / t
+    t, value = whole_job_rate(e0.elapsed_time(e1) / 1000.0, pairs_per_step * args.steps, world,
+                              dist, dev)
 
     # end to end through the public API with host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -260,9 +269,9 @@ def run_ours(args):
         plan.deblend(d, m, drec, batch=B, stream=stream, **kw)
         drec_host.copy_(drec, non_blocking=True)
         torch.cuda.synchronize(dev)
-    te = time.perf_counter() - t0
     barrier()
-    e2e = world * pairs_per_step * e2e_steps / te
+    te, e2e = whole_job_rate(time.perf_counter() - t0, pairs_per_step * e2e_steps, world, dist,
+                             dev)
 
     if rank != 0:
         return
