@@ -305,6 +305,10 @@ long long ashrt_kernel_launches(void);
  *     normalised units, loss sum_c w_c mean (y_c - t_c)^2 with host weights
  *     channel_weight[out_channels] (NULL = 1); *loss (may be NULL) receives
  *     the loss before the step, which synchronises the stream.
+ * The convolutions run on the tensor cores (tcgen05 for the forward pass and
+ * the input gradients, mma.sync for the weight gradients); their device-side
+ * waits are bounded, and one that ran out is reported as ASHRT_ETIMEOUT by the
+ * next synchronising call (ashrt_unet_train_step with a loss, ashrt_unet_get).
  * Device pointers are caller-owned; all return EINVAL on bad sizes.
  */
 typedef struct ashrt_unet ashrt_unet;

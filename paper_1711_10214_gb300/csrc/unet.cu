@@ -620,6 +620,7 @@ struct ashrt_unet {
   float *rms, *lam;
   double* rmsacc;
   bf16* gzb;   // BF16 masked output gradient of the layer being differentiated
+  int* err;    // set by a tensor-core kernel whose bounded wait ran out
   double* loss;
   std::vector<float> lam_h;
 };
@@ -1069,28 +1070,28 @@ void net_forward(ashrt_unet* u, int n, cudaStream_t s, float* head_planar = null
   // encoder
   k_conv_first<<<grid((long long)n * H * W), 256, 0, s>>>(u->x, L[0].wf, B(0), T_(u->e1a, c0), n,
                                                           H, W, 1);
-  conv_mma<3, bf16>(T_(u->e1a, c0), L[1].wn, B(1), T_(u->cat1, c1 + c0, c1), n, H, W, c0, c0, 1, s);
+  conv_mma<3, bf16>(T_(u->e1a, c0), L[1].wn, B(1), T_(u->cat1, c1 + c0, c1), n, H, W, c0, c0, 1, s, u->err);
   k_pool<<<grid((long long)n * H * W / 4 * c0), 256, 0, s>>>(T_(u->cat1, c1 + c0, c1), T_(u->p1, c0), n, H, W, c0);
-  conv_mma<3, bf16>(T_(u->p1, c0), L[2].wn, B(2), T_(u->e2a, c1), n, H / 2, W / 2, c0, c1, 1, s);
-  conv_mma<3, bf16>(T_(u->e2a, c1), L[3].wn, B(3), T_(u->cat2, c2 + c1, c2), n, H / 2, W / 2, c1, c1, 1, s);
+  conv_mma<3, bf16>(T_(u->p1, c0), L[2].wn, B(2), T_(u->e2a, c1), n, H / 2, W / 2, c0, c1, 1, s, u->err);
+  conv_mma<3, bf16>(T_(u->e2a, c1), L[3].wn, B(3), T_(u->cat2, c2 + c1, c2), n, H / 2, W / 2, c1, c1, 1, s, u->err);
   k_pool<<<grid((long long)n * H * W / 16 * c1), 256, 0, s>>>(T_(u->cat2, c2 + c1, c2), T_(u->p2, c1), n, H / 2, W / 2, c1);
-  conv_mma<3, bf16>(T_(u->p2, c1), L[4].wn, B(4), T_(u->e3a, c2), n, H / 4, W / 4, c1, c2, 1, s);
-  conv_mma<3, bf16>(T_(u->e3a, c2), L[5].wn, B(5), T_(u->cat3, c3 + c2, c3), n, H / 4, W / 4, c2, c2, 1, s);
+  conv_mma<3, bf16>(T_(u->p2, c1), L[4].wn, B(4), T_(u->e3a, c2), n, H / 4, W / 4, c1, c2, 1, s, u->err);
+  conv_mma<3, bf16>(T_(u->e3a, c2), L[5].wn, B(5), T_(u->cat3, c3 + c2, c3), n, H / 4, W / 4, c2, c2, 1, s, u->err);
   k_pool<<<grid((long long)n * H * W / 64 * c2), 256, 0, s>>>(T_(u->cat3, c3 + c2, c3), T_(u->p3, c2), n, H / 4, W / 4, c2);
-  conv_mma<3, bf16>(T_(u->p3, c2), L[6].wn, B(6), T_(u->ba, c3), n, H / 8, W / 8, c2, c3, 1, s);
-  conv_mma<3, bf16>(T_(u->ba, c3), L[7].wn, B(7), T_(u->bb, c3), n, H / 8, W / 8, c3, c3, 1, s);
+  conv_mma<3, bf16>(T_(u->p3, c2), L[6].wn, B(6), T_(u->ba, c3), n, H / 8, W / 8, c2, c3, 1, s, u->err);
+  conv_mma<3, bf16>(T_(u->ba, c3), L[7].wn, B(7), T_(u->bb, c3), n, H / 8, W / 8, c3, c3, 1, s, u->err);
   // decoder
   k_up<<<grid((long long)n * H * W / 16 * c3 / 8), 256, 0, s>>>(T_(u->bb, c3), T_(u->cat3, c3 + c2, 0), n, H / 4, W / 4, c3);
-  conv_mma<3, bf16>(T_(u->cat3, c3 + c2), L[8].wn, B(8), T_(u->d3a, c2), n, H / 4, W / 4, c3 + c2, c2, 1, s);
-  conv_mma<3, bf16>(T_(u->d3a, c2), L[9].wn, B(9), T_(u->d3b, c2), n, H / 4, W / 4, c2, c2, 1, s);
+  conv_mma<3, bf16>(T_(u->cat3, c3 + c2), L[8].wn, B(8), T_(u->d3a, c2), n, H / 4, W / 4, c3 + c2, c2, 1, s, u->err);
+  conv_mma<3, bf16>(T_(u->d3a, c2), L[9].wn, B(9), T_(u->d3b, c2), n, H / 4, W / 4, c2, c2, 1, s, u->err);
   k_up<<<grid((long long)n * H * W / 4 * c2 / 8), 256, 0, s>>>(T_(u->d3b, c2), T_(u->cat2, c2 + c1, 0), n, H / 2, W / 2, c2);
-  conv_mma<3, bf16>(T_(u->cat2, c2 + c1), L[10].wn, B(10), T_(u->d2a, c1), n, H / 2, W / 2, c2 + c1, c1, 1, s);
-  conv_mma<3, bf16>(T_(u->d2a, c1), L[11].wn, B(11), T_(u->d2b, c1), n, H / 2, W / 2, c1, c1, 1, s);
+  conv_mma<3, bf16>(T_(u->cat2, c2 + c1), L[10].wn, B(10), T_(u->d2a, c1), n, H / 2, W / 2, c2 + c1, c1, 1, s, u->err);
+  conv_mma<3, bf16>(T_(u->d2a, c1), L[11].wn, B(11), T_(u->d2b, c1), n, H / 2, W / 2, c1, c1, 1, s, u->err);
   k_up<<<grid((long long)n * H * W * c1 / 8), 256, 0, s>>>(T_(u->d2b, c1), T_(u->cat1, c1 + c0, 0), n, H, W, c1);
-  conv_mma<3, bf16>(T_(u->cat1, c1 + c0), L[12].wn, B(12), T_(u->d1a, c0), n, H, W, c1 + c0, c0, 1, s);
-  conv_mma<3, bf16>(T_(u->d1a, c0), L[13].wn, B(13), T_(u->d1b, c0), n, H, W, c0, c0, 1, s);
+  conv_mma<3, bf16>(T_(u->cat1, c1 + c0), L[12].wn, B(12), T_(u->d1a, c0), n, H, W, c1 + c0, c0, 1, s, u->err);
+  conv_mma<3, bf16>(T_(u->d1a, c0), L[13].wn, B(13), T_(u->d1b, c0), n, H, W, c0, c0, 1, s, u->err);
   if (!head_planar || !conv_tc<1, float>(T_(u->d1b, c0), L[14].wn, B(14), T_(head_planar, 1), n, H,
-                                         W, c0, u->cout, 0, nullptr, s, 1)) {
+                                         W, c0, u->cout, 0, u->err, s, 1)) {
     conv_mma<1, float>(T_(u->d1b, c0), L[14].wn, B(14), T_(u->y, u->cout), n, H, W, c0, u->cout,
                        0, s);
     if (head_planar) {
@@ -1263,7 +1264,7 @@ void layer_backward(ashrt_unet* u, Tensor in, Tensor g, Tensor act, const Layer&
   if (Cout <= 16) wgrad_mma_v<1>(a, s);
   else wgrad_mma_v<2>(a, s);
   if (out.p && !conv_tc<3, float>(T_(u->gzb, Cout), l.wtn, nullptr, out, n, H, W, Cout, Cin, 0,
-                                  nullptr, s))
+                                  u->err, s))
     conv<3, float, float>(g, act, l.wt, nullptr, out, n, H, W, Cout, Cin, 0, s);
 }
 
@@ -1411,6 +1412,7 @@ ashrt_status ashrt_unet_create(ashrt_unet** out, int H, int W, int out_channels,
   A(&u->rms, max_batch);
   A(&u->rmsacc, max_batch);
   A(&u->gzb, P0 * c0);
+  A(&u->err, 1);
   A(&u->lam, out_channels);
   A(&u->loss, 1);
   if (e != cudaSuccess) {
@@ -1448,6 +1450,7 @@ ashrt_status ashrt_unet_create(ashrt_unet** out, int H, int W, int out_channels,
   }
   e = cudaMemcpy(u->w, h.data(), off * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(u->am, 0, off * 4);
+  if (e == cudaSuccess) e = cudaMemset(u->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(u->av, 0, off * 4);
   if (e == cudaSuccess) e = cudaMemset(u->g, 0, off * 4);
   if (e == cudaSuccess) e = refresh_bf16_weights(u, 0);
@@ -1479,6 +1482,13 @@ ashrt_status ashrt_unet_get(const ashrt_unet* u, float* params, float* grads, lo
     return ASHRT_EINVAL;
   }
   cudaError_t e = cudaDeviceSynchronize();
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&err, u->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && err) {
+    cudaMemset(u->err, 0, sizeof(int));
+    set_error("ashrt_unet_get: a tensor-core kernel's bounded wait ran out in an earlier call");
+    return ASHRT_ETIMEOUT;
+  }
   if (e == cudaSuccess && params) e = cudaMemcpy(params, u->w, n * 4, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && grads) e = cudaMemcpy(grads, u->g, n * 4, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
@@ -1559,13 +1569,20 @@ ashrt_status ashrt_unet_train_step(ashrt_unet* u, const float* x, const float* t
     refresh_bf16_weights(u, s);
   }
   cudaError_t e = cudaGetLastError();
+  int err = 0;
   if (e == cudaSuccess && loss_out) {
     e = cudaMemcpyAsync(loss_out, u->loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, u->err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
   if (e != cudaSuccess) {
     set_error("ashrt_unet_train_step: %s", cudaGetErrorString(e));
     return ASHRT_ECUDA;
+  }
+  if (err) {
+    cudaMemsetAsync(u->err, 0, sizeof(int), s);
+    set_error("ashrt_unet_train_step: a tensor-core kernel's bounded wait ran out");
+    return ASHRT_ETIMEOUT;
   }
   return ASHRT_OK;
 }
