@@ -86,6 +86,9 @@ stolt_adj_rows(RowArgs a) {
     __syncthreads();
     const int km = __ldg(a.kmin + iv * a.Lh + l);
     const float2* phj = SHIFT ? a.phase + (long long)jt * N : nullptr;
+    // the bins this thread gathers, j = tid + T s, are exactly the inputs of
+    // its first inverse-FFT butterfly: they stay in registers
+    float4 accs[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int j = tid + T * s;
@@ -111,16 +114,18 @@ stolt_adj_rows(RowArgs a) {
           }
         }
       }
-      buf[swz4(j)] = acc;
+      accs[s] = acc;
     }
-    __syncthreads();
+    // first pass from the registers (its barrier also ends every thread's
+    // reads of the tap and run-start rows, which are then restaged)
+    row_first_pass<+1, N>(buf, accs, tid);
     if (p + 1 < a.P) {
       const int ivn = iv + 1 == a.nv ? 0 : iv + 1;
       stage_taps(stap, trow + ivn * tstep, a.taps_ld, tid, T);
       stage_u16(ks, krow + ivn * kstep, a.ks_ld, tid, T);
       cp_async_commit();
     }
-    row_pass_range<+1, LOGN, 0, S::NPASS - 1>(buf, a.tw, tid);
+    row_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw, tid);
     const long long o = (long long)p * a.x_panel;
     row_last_pass_global<+1, LOGN>(buf, a.tw, tid, xA + o, hasB ? xB + o : nullptr, a.nt);
     if (++iv == a.nv) {
