@@ -289,8 +289,8 @@ def run_ours(args):
     achieved = flops / per_launch_s / 1e12
     # DRAM bytes per launch of the dominant kernel, from one ncu capture of the
     # 8-gather launch of the same kernel (dram__bytes_read.sum +
-    # dram__bytes_write.sum = 633.8 MB), scaled by the gathers per launch
-    traffic = {"stolt_adj_rows": 633.8e6 / 8}.get(dom)
+    # dram__bytes_write.sum = 627.7 MB), scaled by the gathers per launch
+    traffic = {"stolt_adj_rows": 627.7e6 / 8}.get(dom)
     traffic = traffic * B if traffic is not None else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
