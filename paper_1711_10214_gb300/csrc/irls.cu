@@ -128,9 +128,9 @@ __global__ void k_resid(const float* __restrict__ d, const float* __restrict__ y
 
 // ---- radix select of order statistics over the live samples of each gather.
 // sel layout per gather (kSelStride words): [0,256) histogram, 256 prefix,
-// 257 rank, 258 key of rank k1, 259 key of rank k2, 260 count of keys <= k1-key.
-constexpr int SEL_PREFIX = 256, SEL_RANK = 257, SEL_K1 = 258, SEL_K2 = 259, SEL_LE = 260,
-              SEL_MINGT = 261;
+// 257 rank, 260 count of keys equal to the rank-k1 key at or after its rank,
+// 261 smallest key above it.
+constexpr int SEL_PREFIX = 256, SEL_RANK = 257, SEL_LE = 260, SEL_MINGT = 261;
 
 // value transform: mode 0 -> x, mode 1 -> |x - med|
 __device__ __forceinline__ float sel_value(float x, int mode, double med) {

@@ -33,8 +33,6 @@ template <typename T>
 __device__ __forceinline__ float ld_f(const T* p, long long i);
 template <>
 __device__ __forceinline__ float ld_f<float>(const float* p, long long i) { return p[i]; }
-template <>
-__device__ __forceinline__ float ld_f<bf16>(const bf16* p, long long i) { return __bfloat162float(p[i]); }
 
 template <typename T>
 __device__ __forceinline__ void st_f(T* p, long long i, float v);
@@ -50,7 +48,7 @@ struct Tensor {        // a channel slice of an NHWC buffer
 };
 
 struct ConvArgs {
-  Tensor in;           // input (bf16 activations or fp32 gradients)
+  Tensor in;           // input: fp32 gradients (the CUDA-core fallback of the backward)
   Tensor mask;         // bf16 activation: multiply input by (mask > 0), or p == nullptr
   const bf16* w;       // [K*K][Cin][Cout]
   const float* bias;   // [Cout] or nullptr
