@@ -52,8 +52,8 @@ typedef struct ashrt_plan ashrt_plan;
 
 /* Operator options (ch. 5 "zero padding"; ch. 4 wavelet C; ch. 5 band limit). */
 typedef struct {
-  int pad_t;              /* Nt = next power of two >= pad_t * nt (default 2) */
-  int pad_x;              /* Nx = next power of two >= pad_x * nx (default 2) */
+  int pad_t;              /* Nt = next power of two >= pad_t * nt (default 2), at least 64 */
+  int pad_x;              /* Nx = next power of two >= pad_x * nx (default 2), at least 16 */
   float fmax_hz;          /* > 0: zero |f| > fmax in both directions; 0 = none */
   float wavelet_peak_hz;  /* > 0: apply the zero-phase Ricker amplitude spectrum
                              W(f) = (f/fp)^2 exp(1 - (f/fp)^2) as C (forward) and
