@@ -246,6 +246,13 @@ typedef struct ashrt_batch ashrt_batch;
 ashrt_status ashrt_batch_create(ashrt_batch** out, int nt, const int* nx_per_gather, int ngather,
                                 double dt, double dx, const float* velocities, int nv,
                                 const float* t0_shifts, int nt0, const ashrt_opts* opts);
+/* The same for gathers of uneven sample counts too: gather g is [nx_g][nt_g]
+ * (model [nt0][nv][nx_g][nt_g]) at the packed offsets sum_{h<g} nx_h nt_h
+ * (times P for the model); classes are formed per (nt, Nx). */
+ashrt_status ashrt_batch_create_uneven(ashrt_batch** out, const int* nt_per_gather,
+                                       const int* nx_per_gather, int ngather, double dt, double dx,
+                                       const float* velocities, int nv, const float* t0_shifts,
+                                       int nt0, const ashrt_opts* opts);
 void ashrt_batch_destroy(ashrt_batch* batch);
 /* Number of Nx classes, packed data / model element counts, device bytes held. */
 ashrt_status ashrt_batch_info(const ashrt_batch* batch, int* n_classes, long long* data_elems,

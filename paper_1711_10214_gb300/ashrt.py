@@ -86,6 +86,10 @@ def load():
     lib.ashrt_batch_create.argtypes = [P(c_void_p), c_int, P(c_int), c_int, c_double, c_double,
                                        P(c_float), c_int, P(c_float), c_int, P(AshrtOpts)]
     lib.ashrt_batch_create.restype = c_int
+    lib.ashrt_batch_create_uneven.argtypes = [P(c_void_p), P(c_int), P(c_int), c_int, c_double,
+                                              c_double, P(c_float), c_int, P(c_float), c_int,
+                                              P(AshrtOpts)]
+    lib.ashrt_batch_create_uneven.restype = c_int
     lib.ashrt_batch_destroy.argtypes = [c_void_p]
     lib.ashrt_batch_destroy.restype = None
     lib.ashrt_batch_info.argtypes = [c_void_p, P(c_int), P(ctypes.c_longlong),
@@ -311,7 +315,8 @@ def _reports(reps):
 
 
 class Batch:
-    """Uneven batch of gathers (see ashrt_batch_create in include/ashrt.h)."""
+    """Uneven batch of gathers (see ashrt_batch_create in include/ashrt.h).
+    nt is one sample count for every gather or one per gather."""
 
     def __init__(self, nt, nx_per_gather, dt, dx, velocities, t0s=None, pad_t=2, pad_x=2,
                  fmax_hz=0.0, wavelet_peak_hz=0.0, max_resident=64, with_solver=False):
@@ -330,16 +335,24 @@ class Batch:
             nt0 = self._t0.size
         h = c_void_p()
         self._h = None
-        _check(lib.ashrt_batch_create(ctypes.byref(h), int(nt), self.nx.ctypes.data_as(
-            ctypes.POINTER(c_int)), self.nx.size, float(dt), float(dx), vp, self._v.size, tp, nt0,
-            ctypes.byref(o)))
+        ip = lambda a: a.ctypes.data_as(ctypes.POINTER(c_int))
+        if np.ndim(nt) == 0:
+            _check(lib.ashrt_batch_create(ctypes.byref(h), int(nt), ip(self.nx), self.nx.size,
+                                          float(dt), float(dx), vp, self._v.size, tp, nt0,
+                                          ctypes.byref(o)))
+        else:
+            self._nts = np.ascontiguousarray(np.asarray(nt, dtype=np.int32))
+            _check(lib.ashrt_batch_create_uneven(ctypes.byref(h), ip(self._nts), ip(self.nx),
+                                                 self.nx.size, float(dt), float(dx), vp,
+                                                 self._v.size, tp, nt0, ctypes.byref(o)))
         self._h = h.value
         ncls, de, me, ws = c_int(), ctypes.c_longlong(), ctypes.c_longlong(), c_size_t()
         _check(lib.ashrt_batch_info(self._h, ctypes.byref(ncls), ctypes.byref(de),
                                     ctypes.byref(me), ctypes.byref(ws)))
         self.n_classes, self.data_elems, self.model_elems = ncls.value, de.value, me.value
         self.workspace_bytes = ws.value
-        self.nt, self.P = int(nt), self._v.size * nt0
+        self.nt = int(nt) if np.ndim(nt) == 0 else [int(v) for v in nt]
+        self.P = self._v.size * nt0
 
     def forward(self, m, d, stream=None):
         _check(load().ashrt_batch_forward(self._h, _ptr(m), _ptr(d), _stream(stream)))

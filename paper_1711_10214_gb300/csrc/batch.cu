@@ -1,4 +1,4 @@
-// Batches of receiver gathers with uneven trace counts.
+// Batches of receiver gathers with uneven trace and sample counts.
 //
 // The Stolt operator of a gather with nx traces is the operator of a wider
 // gather with the same padded width Nx (= next power of two >= pad_x nx)
@@ -11,13 +11,16 @@
 // from the unknowns (apex mask 0: W_m^-1 = 0).  So gathers are grouped by Nx
 // class, packed into a resident class batch of width nxc (the widest gather of
 // the class) with zero padding, and solved together by one plan per class;
-// the classes run concurrently on their own streams.  Gather streams larger
-// than the resident batch are processed chunk by chunk.
+// the classes run concurrently on their own streams.  Gathers of different
+// sample counts nt fall into different classes (a plan's time grid is its
+// own).  Gather streams larger than the resident batch are processed chunk
+// by chunk.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -76,13 +79,13 @@ int next_pow2(int n) {
 }  // namespace
 
 struct ashrt_batch {
-  int nt = 0, ngather = 0, P = 0;
-  std::vector<int> nx;
+  int ngather = 0, P = 0;
+  std::vector<int> nx, nt;
   std::vector<long long> doff, moff;   // packed element offsets of each gather
   long long data_elems = 0, model_elems = 0;
   size_t ws_bytes = 0;
   struct Class {
-    int Nx = 0, nxc = 0, mb = 0;
+    int nt = 0, Nx = 0, nxc = 0, mb = 0;
     std::vector<int> gathers;
     ashrt_plan* plan = nullptr;
     float *d = nullptr, *m = nullptr, *drec = nullptr, *tmask = nullptr;
@@ -120,6 +123,19 @@ ashrt_status ashrt_batch_create(ashrt_batch** out, int nt, const int* nx_per_gat
     set_error("ashrt_batch_create: need out, nx_per_gather and ngather >= 1");
     return ASHRT_EINVAL;
   }
+  std::vector<int> nts(ngather, nt);
+  return ashrt_batch_create_uneven(out, nts.data(), nx_per_gather, ngather, dt, dx, velocities, nv,
+                                   t0_shifts, nt0, opts);
+}
+
+ashrt_status ashrt_batch_create_uneven(ashrt_batch** out, const int* nt_per_gather,
+                                       const int* nx_per_gather, int ngather, double dt, double dx,
+                                       const float* velocities, int nv, const float* t0_shifts,
+                                       int nt0, const ashrt_opts* opts) {
+  if (!out || !nt_per_gather || !nx_per_gather || ngather < 1) {
+    set_error("ashrt_batch_create: need out, nt_per_gather, nx_per_gather and ngather >= 1");
+    return ASHRT_EINVAL;
+  }
   *out = nullptr;
   ashrt_opts o;
   ashrt_default_opts(&o);
@@ -127,30 +143,33 @@ ashrt_status ashrt_batch_create(ashrt_batch** out, int nt, const int* nx_per_gat
   if (o.pad_x <= 0) o.pad_x = 2;
   if (o.max_batch <= 0) o.max_batch = 64;
   for (int g = 0; g < ngather; ++g)
-    if (nx_per_gather[g] < 2) {
-      set_error("ashrt_batch_create: gather %d has %d traces (need >= 2)", g, nx_per_gather[g]);
+    if (nx_per_gather[g] < 2 || nt_per_gather[g] < 2) {
+      set_error("ashrt_batch_create: gather %d has %d traces of %d samples (need >= 2 each)", g,
+                nx_per_gather[g], nt_per_gather[g]);
       return ASHRT_EINVAL;
     }
   ashrt_batch* b = new ashrt_batch();
-  b->nt = nt;
   b->ngather = ngather;
   b->P = nv * (t0_shifts ? nt0 : 1);
   b->nx.assign(nx_per_gather, nx_per_gather + ngather);
+  b->nt.assign(nt_per_gather, nt_per_gather + ngather);
   b->doff.resize(ngather);
   b->moff.resize(ngather);
   for (int g = 0; g < ngather; ++g) {
     b->doff[g] = b->data_elems;
     b->moff[g] = b->model_elems;
-    b->data_elems += (long long)b->nx[g] * nt;
-    b->model_elems += (long long)b->P * b->nx[g] * nt;
+    b->data_elems += (long long)b->nx[g] * b->nt[g];
+    b->model_elems += (long long)b->P * b->nx[g] * b->nt[g];
   }
-  // Nx classes
-  std::map<int, std::vector<int>> by;
-  for (int g = 0; g < ngather; ++g) by[next_pow2(o.pad_x * b->nx[g])].push_back(g);
+  // classes: one per (nt, padded width Nx)
+  std::map<std::pair<int, int>, std::vector<int>> by;
+  for (int g = 0; g < ngather; ++g)
+    by[std::make_pair(b->nt[g], next_pow2(o.pad_x * b->nx[g]))].push_back(g);
   ashrt_status st = ASHRT_OK;
   for (auto& kv : by) {
     ashrt_batch::Class c;
-    c.Nx = kv.first;
+    c.nt = kv.first.first;
+    c.Nx = kv.first.second;
     c.gathers = kv.second;
     for (int g : c.gathers) c.nxc = std::max(c.nxc, b->nx[g]);
     c.mb = std::min<int>((int)c.gathers.size(), o.max_batch);
@@ -160,8 +179,8 @@ ashrt_status ashrt_batch_create(ashrt_batch** out, int nt, const int* nx_per_gat
     ashrt_opts oc = o;
     oc.max_batch = c.mb;
     // pad_x chosen so that the class plan has exactly this class's Nx
-    st = ashrt_plan_create(&c.plan, nt, c.nxc, dt, dx, velocities, nv, nullptr, 0, t0_shifts, nt0,
-                           &oc);
+    st = ashrt_plan_create(&c.plan, c.nt, c.nxc, dt, dx, velocities, nv, nullptr, 0, t0_shifts,
+                           nt0, &oc);
     if (st != ASHRT_OK) break;
     int Nx = 0;
     ashrt_plan_info(c.plan, nullptr, &Nx, nullptr, &b->ws_bytes);
@@ -170,7 +189,7 @@ ashrt_status ashrt_batch_create(ashrt_batch** out, int nt, const int* nx_per_gat
       st = ASHRT_EINTERNAL;
       break;
     }
-    const size_t de = (size_t)c.mb * c.nxc * nt, me = de * b->P;
+    const size_t de = (size_t)c.mb * c.nxc * c.nt, me = de * b->P;
     const size_t n = c.gathers.size();
     cudaError_t e = cudaMalloc(&c.d, de * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c.drec, de * 4);
@@ -279,9 +298,10 @@ ashrt_status ashrt_batch_forward(ashrt_batch* b, const float* m, float* d, void*
     set_error("ashrt_batch_forward: NULL argument");
     return ASHRT_EINVAL;
   }
-  const int nt = b->nt, P = b->P;
+  const int P = b->P;
   return for_each_chunk(b, (cudaStream_t)stream,
                         [&](ashrt_batch::Class& c, int first, int count, cudaStream_t s) {
+    const int nt = c.nt;
     const long long per_m = (long long)P * c.nxc * nt, per_d = (long long)c.nxc * nt;
     k_pack<<<pack_grid(per_m, count), 256, 0, s>>>(m, c.m, c.moff_dev + first, c.nx_dev + first,
                                                     c.nxc, nt, P, c.tmask);
@@ -300,9 +320,10 @@ ashrt_status ashrt_batch_adjoint(ashrt_batch* b, const float* d, float* m, void*
     set_error("ashrt_batch_adjoint: NULL argument");
     return ASHRT_EINVAL;
   }
-  const int nt = b->nt, P = b->P;
+  const int P = b->P;
   return for_each_chunk(b, (cudaStream_t)stream,
                         [&](ashrt_batch::Class& c, int first, int count, cudaStream_t s) {
+    const int nt = c.nt;
     const long long per_m = (long long)P * c.nxc * nt, per_d = (long long)c.nxc * nt;
     k_pack<<<pack_grid(per_d, count), 256, 0, s>>>(d, c.d, c.doff_dev + first, c.nx_dev + first,
                                                     c.nxc, nt, 1, c.tmask);
@@ -334,10 +355,11 @@ ashrt_status ashrt_batch_deblend(ashrt_batch* b, const float* d, float* m, float
       set_error("ashrt_batch_deblend: the batch was created without with_solver");
       return ASHRT_EINVAL;
     }
-  const int nt = b->nt, P = b->P;
+  const int P = b->P;
   std::vector<irls_report> rep;
   return for_each_chunk(b, (cudaStream_t)stream,
                         [&](ashrt_batch::Class& c, int first, int count, cudaStream_t s) {
+    const int nt = c.nt;
     const long long per_m = (long long)P * c.nxc * nt, per_d = (long long)c.nxc * nt;
     k_pack<<<pack_grid(per_d, count), 256, 0, s>>>(d, c.d, c.doff_dev + first, c.nx_dev + first,
                                                     c.nxc, nt, 1, c.tmask);

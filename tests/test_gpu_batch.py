@@ -107,3 +107,41 @@ def test_recorded_graph_solve_matches_direct(lib):
         assert a["applies_fwd"] == c["applies_fwd"] and a["outer_done"] == c["outer_done"]
         np.testing.assert_allclose(a["misfit"], c["misfit"], rtol=1e-5)
     plan.close()
+
+
+def test_uneven_sample_counts(lib):
+    """Gathers of different nt and nx in one batch: classes per (nt, Nx);
+    operator parity and the deblend of every gather as if alone."""
+    import torch
+    from paper_1711_10214_gb300 import ashrt
+    nts, nxs, v = [64, 80, 64, 72, 80], [13, 20, 9, 17, 11], [1600.0, 2500.0]
+    b = ashrt.Batch(nts, nxs, DT, DX, v, with_solver=True, max_resident=2)
+    assert b.n_classes == 4     # (nt, Nx): (64, 32) twice, (80, 64), (72, 64), (80, 32)
+    rng = np.random.default_rng(24)
+    ms = [rng.standard_normal((2, nx, nt)) for nt, nx in zip(nts, nxs)]
+    ds = [rng.standard_normal((nx, nt)) for nt, nx in zip(nts, nxs)]
+    mflat = np.concatenate([m.ravel() for m in ms]).astype(np.float32)
+    dflat = np.concatenate([d.ravel() for d in ds]).astype(np.float32)
+    assert (b.model_elems, b.data_elems) == (mflat.size, dflat.size)
+    dev = torch.device("cuda:0")
+    mg, dg = torch.from_numpy(mflat).to(dev), torch.from_numpy(dflat).to(dev)
+    od, om = torch.empty_like(dg), torch.empty_like(mg)
+    b.forward(mg, od)
+    b.adjoint(dg, om)
+    mrec, drec = torch.empty_like(mg), torch.empty_like(dg)
+    reps = b.deblend(dg, mrec, drec, p=1.0, q=1.0, n_outer=2, n_cg=4)
+    torch.cuda.synchronize()
+    od_l = _split(od.cpu().numpy().astype(np.float64), [(nx, nt) for nt, nx in zip(nts, nxs)])
+    om_l = _split(om.cpu().numpy().astype(np.float64), [(2, nx, nt) for nt, nx in zip(nts, nxs)])
+    rec = _split(drec.cpu().numpy().astype(np.float64), [(nx, nt) for nt, nx in zip(nts, nxs)])
+    for i, (nt, nx) in enumerate(zip(nts, nxs)):
+        g = stolt.Geometry(nt, nx, DT, DX, v)
+        m32 = ms[i].astype(np.float32).astype(np.float64).reshape(g.model_shape)
+        d32 = ds[i].astype(np.float32).astype(np.float64)
+        assert _rel(od_l[i], stolt.forward(g, m32)) <= 1e-4, i
+        assert _rel(om_l[i].reshape(g.model_shape), stolt.adjoint(g, d32)) <= 1e-4, i
+        mo, rep = irls.irls(lambda x: stolt.forward(g, x), lambda r: stolt.adjoint(g, r), d32,
+                            n_outer=2, n_cg=4, p=1, q=1)
+        assert _rel(rec[i], stolt.forward(g, mo)) <= 1e-3, i
+        np.testing.assert_allclose(reps[i]["misfit"], rep["misfit"], rtol=1e-3)
+    b.close()
