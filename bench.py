@@ -47,6 +47,9 @@ def _args():
     ap.add_argument("--batch", type=int, default=B,
                     help="gathers per call (the deblend workload is 64; smaller batches are "
                          "for profiling captures)")
+    ap.add_argument("--rows-variant", type=int, default=0,
+                    help="ops mode: row-kernel variant 1..5 (0: the plan's default; see "
+                         "ashrt_plan_set_variant)")
     return ap.parse_args()
 
 
@@ -289,8 +292,9 @@ def run_ours(args):
     achieved = flops / per_launch_s / 1e12
     # DRAM bytes per launch of the dominant kernel, from one ncu capture of the
     # 8-gather launch of the same kernel (dram__bytes_read.sum +
-    # dram__bytes_write.sum = 627.7 MB), scaled by the gathers per launch
-    traffic = {"stolt_adj_rows": 627.7e6 / 8}.get(dom)
+    # dram__bytes_write.sum = 672.2 MB for the radix-8 adjoint with its source
+    # table), scaled by the gathers per launch
+    traffic = {"stolt_adj_rows": 672.2e6 / 8}.get(dom)
     traffic = traffic * B if traffic is not None else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -327,6 +331,8 @@ def run_ops(args):
     nb = args.batch
     v = synth.velocity_scan(1400.0, 3500.0, NV)
     plan = ashrt.Plan(NT, NX, DT, DX, v, wavelet_peak_hz=F_PEAK, max_batch=nb)
+    if args.rows_variant:
+        plan.set_variant(args.rows_variant, 16)
     g = torch.Generator(device=dev).manual_seed(0)
     m = torch.randn((nb,) + plan.model_shape, device=dev, generator=g)
     d = torch.randn((nb, NX, NT), device=dev, generator=g)
@@ -346,7 +352,8 @@ def run_ops(args):
     ashrt.profile_enable(False)
     prof = ashrt.profile_read()
     t = e0.elapsed_time(e1) / 1000.0
-    print(json.dumps({"mode": "ops", "batch": nb, "pairs_per_s": nb * args.steps / t,
+    print(json.dumps({"mode": "ops", "batch": nb, "rows_variant": args.rows_variant or "default",
+                      "pairs_per_s": nb * args.steps / t,
                       "ms_per_pair_call": 1000.0 * t / args.steps,
                       "kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items()}}),
           flush=True)

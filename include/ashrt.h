@@ -214,8 +214,12 @@ ashrt_status robust_irls_deblend(const ashrt_plan* plan, const float* d_dev, flo
 /*
  * Autotuner (no counterpart in the paper): times forward+adjoint pairs of
  * `batch` gathers on the plan's sizes for each kernel variant -- the row
- * kernels' register cap (1, 2 or 3 resident CTAs per SM for Nt 512..2048) and
- * the trace-axis FFT column tile (16 or 8 columns for Nx <= 512) -- and keeps
+ * kernels' form (rows_minb 1, 2 or 3: radix-8 transforms with a register cap
+ * for that many resident CTAs per SM, Nt 512..2048; for Nt 1024..4096 also
+ * 4: radix-16 forward (three shared-memory passes per transform instead of
+ * four) with the radix-8 adjoint, and 5: radix-16 both; the default is 4
+ * where it applies, else 3) and the trace-axis FFT column tile (16 or 8
+ * columns for Nx <= 512) -- and keeps
  * the fastest in the plan.  With cache_path (a JSON-lines file, one object per
  * device and problem shape) a cached choice is reused without timing and new
  * choices are appended.  Allocates and frees temporary buffers; synchronises.
@@ -224,12 +228,15 @@ ashrt_status robust_irls_deblend(const ashrt_plan* plan, const float* d_dev, flo
  */
 ashrt_status ashrt_plan_autotune(ashrt_plan* plan, int batch, const char* cache_path,
                                  int* rows_minb, int* xfft_cols);
-/* Sets the variants directly (rows_minb 1..3, xfft_cols 8 or 16); variants that
- * do not apply to the plan's sizes fall back to the default kernel. */
+/* Sets the variants directly (rows_minb 1..5, xfft_cols 8 or 16); register
+ * caps and column tiles that do not apply to the plan's sizes fall back to the
+ * default kernel; rows_minb 4 or 5 on an Nt other than 1024, 2048 or 4096 is
+ * ASHRT_EINVAL. */
 ashrt_status ashrt_plan_set_variant(ashrt_plan* plan, int rows_minb, int xfft_cols);
 
 /*
- * Batches of gathers with uneven trace counts (all with the same nt).  The
+ * Batches of gathers with uneven trace counts (ashrt_batch_create: all with
+ * the same nt; ashrt_batch_create_uneven below: uneven nt too).  The
  * gathers are independent (ch. 1: separation gather by gather is parallel
  * work); packed layouts concatenate them:
  *   data   : gather g is [nx_g][nt] at element offset nt * sum_{h<g} nx_h

@@ -1,5 +1,6 @@
 // Autotuner: picks the kernel variants of a plan (the row kernels' register
-// cap, i.e. resident CTAs per SM, and the trace-axis FFT column tile) by timing
+// cap, i.e. resident CTAs per SM, or their radix-16 form, and the trace-axis
+// FFT column tile) by timing
 // forward+adjoint operator pairs on the plan's own sizes, and keeps the choice
 // in a JSON-lines cache keyed by device and problem shape.
 #include <cuda_runtime.h>
@@ -123,6 +124,10 @@ extern "C" ashrt_status ashrt_plan_autotune(ashrt_plan* p, int batch, const char
 
   std::vector<int> minbs = {3};
   if (p->logNt >= 9 && p->logNt <= 11) minbs = {3, 2, 1};
+  if (rows16_supported(p->logNt) && p->tw_t16) {
+    minbs.push_back(4);
+    minbs.push_back(5);
+  }
   std::vector<int> colss = {16};
   if (p->logNx <= 9) colss = {16, 8};
   double best = 1e30;
@@ -162,8 +167,12 @@ extern "C" ashrt_status ashrt_plan_autotune(ashrt_plan* p, int batch, const char
 }
 
 extern "C" ashrt_status ashrt_plan_set_variant(ashrt_plan* p, int rows_minb, int xfft_cols) {
-  if (!p || rows_minb < 1 || rows_minb > 3 || (xfft_cols != 8 && xfft_cols != 16)) {
-    set_error("ashrt_plan_set_variant: need a plan, rows_minb in 1..3, xfft_cols 8 or 16");
+  if (!p || rows_minb < 1 || rows_minb > 5 || (xfft_cols != 8 && xfft_cols != 16)) {
+    set_error("ashrt_plan_set_variant: need a plan, rows_minb in 1..5, xfft_cols 8 or 16");
+    return ASHRT_EINVAL;
+  }
+  if (rows_minb >= 4 && !p->tw_t16) {
+    set_error("ashrt_plan_set_variant: the radix-16 row kernels (4, 5) need Nt = 1024, 2048 or 4096");
     return ASHRT_EINVAL;
   }
   p->rows_minb = rows_minb;

@@ -59,22 +59,29 @@ struct RowArgs {
   int nt = 0, ld = 0, Lh = 0, P = 0, nv = 0, nt0 = 0, Nt = 0;
   long long x_batch = 0, x_panel = 0, y_batch = 0;
   const float2* tw = nullptr;      // base twiddles of length Nt
+  const float2* tw16 = nullptr;    // the same for the radix-16 schedule (stolt_r16.cu), or null
   const float* wt = nullptr;       // [Nt] spectral weight W(w)/(Nt Nx), 0 at unmapped bins
   const int* kmin = nullptr;       // [nv][Lh] first mapped |k| (host FP64 cone rule)
   const float2* acone = nullptr;   // [nv][Lh] cone parameter a as (hi, lo) floats
   const unsigned* taps = nullptr;  // [nv][Lh][taps_ld] Stolt taps of |k| (see tap_word)
   int taps_ld = 0;                 // words per (v, l) row: Nt/2 + 1 rounded up to 4
-  const unsigned short* ks = nullptr;  // [nv][Lh][ks_ld] adjoint run starts (see build_ks_rows)
-  int ks_ld = 0;                       // entries per (v, l) row: Nt/2 + 2 rounded up to 8
+  const uint2* atab = nullptr;     // [nv][Lh][atab_ld] adjoint source table (see build_adj_table)
+  int atab_ld = 0;                 // entries per (v, l) row: Nt/2 + 1 rounded up to 2
   const float2* phase = nullptr;   // [nt0][Nt] exp(-i w tau0), or null (tau0 == 0)
   int batch = 0;
-  int minb = 3;                    // register-cap variant (resident CTAs per SM): 1, 2, 3
+  int minb = 3;                    // variant: 1, 2, 3 radix-8 kernels capped for that many
+                                   // resident CTAs per SM; 4 radix-16 forward, radix-8
+                                   // adjoint; 5 radix-16 both (4 and 5 need tw16)
 };
 
 cudaError_t launch_xfft_r2c(const XfftArgs& a, cudaStream_t s);
 cudaError_t launch_xfft_c2r(const XfftArgs& a, cudaStream_t s);
 cudaError_t launch_stolt_fwd_rows(const RowArgs& a, cudaStream_t s);
 cudaError_t launch_stolt_adj_rows(const RowArgs& a, cudaStream_t s);
+// Radix-16 row kernels (Nt = 1024, 2048, 4096 only; see stolt_r16.cu).
+bool rows16_supported(int logNt);
+cudaError_t launch_stolt_fwd_rows16(const RowArgs& a, cudaStream_t s);
+cudaError_t launch_stolt_adj_rows16(const RowArgs& a, cudaStream_t s);
 
 // Stolt tap table: one 32-bit word per (velocity, k_x index l, |k|), |k| in
 // [0, Nt/2].  Mapped bins hold (floor(u) << 20) | round(frac(u) 2^20) with
@@ -84,17 +91,26 @@ constexpr unsigned kTapInvalid = 0xffffffffu;
 inline int taps_row_len(int Nt) { return ((Nt / 2 + 1) + 3) & ~3; }
 void build_tap_rows(const float* velocities, int nv, int Nt, int Nx, int Lh, double dt, double dx,
                     unsigned* taps, int* kmin, float2* acone);
-// Run starts of the transposed map, one u16 row per (velocity, l): ks[J] is
-// the first |k| >= kmin whose tap floor index (word >> 20) is >= J, or Nt/2 if
-// none, for J in [0, Nt/2] (taken from the tap words, so both directions of
-// the map use the same indices).  Rows whose kmin >= Nt/2 are left 0.
-inline int ks_row_len(int Nt) { return ((Nt / 2 + 2) + 7) & ~7; }
-void build_ks_rows(const unsigned* taps, const int* kmin, int nv, int Lh, int Nt,
-                   unsigned short* ks);
+// Source table of the transposed map (the adjoint's gather), one row per
+// (velocity, l), entries J in [0, Nt/2].  With ks[J] the first |k| >= kmin
+// whose tap floor index (word >> 20) is >= J, bin J of the w_tau spectrum
+// takes (1 - f(kB)) D(kB) from its primary source kB = ks[J] when
+// floor(u(kB)) = J, and f(kB - 1) D(kB - 1) from its secondary source
+// kB - 1 when floor(u(kB - 1)) = J - 1, f being the tap fraction.  Since
+// u(k + 1) - u(k) = (2k + 1) / (u(k + 1) + u(k)) >= 1, floor(u) is strictly
+// increasing in k: a bin has at most one source of each kind.  Entry
+// x = frac20(kB) | kB << 20, y = frac20(kB - 1) | has_primary << 20 |
+// has_secondary << 21 (both fractions and indices taken from the tap words,
+// so both directions of the map use the same taps).  Rows with
+// kmin >= Nt/2 are zero.  Returns false if a bin had two sources of one kind.
+inline int atab_row_len(int Nt) { return ((Nt / 2 + 1) + 1) & ~1; }
+bool build_adj_table(const unsigned* taps, const int* kmin, int nv, int Lh, int Nt, uint2* atab);
 
-// Twiddle tables in the layout the device passes expect (see common.cuh).
-int twiddle_table_len(int logn);
-void build_twiddle_table(int logn, float2* out);
+// Twiddle tables in the layout the device passes expect (see common.cuh):
+// radix 2^lr passes while lr or more factors of two remain, then one smaller
+// radix (lr = 3 for the radix-8 kernels, 4 for the radix-16 row kernels).
+int twiddle_table_len(int logn, int lr = 3);
+void build_twiddle_table(int logn, float2* out, int lr = 3);
 
 void set_error(const char* fmt, ...);
 
@@ -139,16 +155,17 @@ struct ashrt_plan {
   int with_solver = 0;
   ashrt_opts opts{};
   bool shift = false;        // any nonzero tau0
-  int rows_minb = 3;         // kernel variants (autotuned; see ashrt_plan_autotune)
+  int rows_minb = 3;         // row-kernel variant 1..5 (autotuned; see ashrt_plan_autotune)
   int xfft_cols = 16;
   // device tables
   float2* tw_t = nullptr;
+  float2* tw_t16 = nullptr;  // radix-16 schedule of length Nt (rows16_supported), else null
   float2* tw_x = nullptr;
   float* wt = nullptr;
   int* kmin = nullptr;
   float2* acone = nullptr;
   unsigned* taps = nullptr;
-  unsigned short* ks = nullptr;
+  uint2* atab = nullptr;
   float2* phase = nullptr;
   // workspace
   float2* X = nullptr;       // [max_batch][P][Lh][ld]

@@ -32,22 +32,22 @@ static int ilog2_ceil(int n) {
 }
 
 // Base twiddles exp(-2 pi i k / (Ns R)), k < Ns, for every pass of a
-// length-2^logn Stockham schedule (radix 8 passes, then one radix 2 or 4).
-int twiddle_table_len(int logn) {
-  int n8 = logn / 3, rl = 1 << (logn % 3), np = n8 + (rl > 1 ? 1 : 0);
+// length-2^logn Stockham schedule (radix 2^lr passes, then one smaller radix).
+int twiddle_table_len(int logn, int lr) {
+  int nf = logn / lr, rl = 1 << (logn % lr), np = nf + (rl > 1 ? 1 : 0);
   int len = 0, ns = 1;
   for (int q = 0; q < np; ++q) {
     len += ns;
-    ns *= (q < n8 ? 8 : rl);
+    ns *= (q < nf ? (1 << lr) : rl);
   }
   return len;
 }
 
-void build_twiddle_table(int logn, float2* out) {
-  int n8 = logn / 3, rl = 1 << (logn % 3), np = n8 + (rl > 1 ? 1 : 0);
+void build_twiddle_table(int logn, float2* out, int lr) {
+  int nf = logn / lr, rl = 1 << (logn % lr), np = nf + (rl > 1 ? 1 : 0);
   int off = 0, ns = 1;
   for (int q = 0; q < np; ++q) {
-    const int R = q < n8 ? 8 : rl;
+    const int R = q < nf ? (1 << lr) : rl;
     for (int k = 0; k < ns; ++k) {
       const double ang = -2.0 * M_PI * (double)k / (double)(ns * R);
       out[off + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
@@ -98,21 +98,33 @@ void build_tap_rows(const float* velocities, int nv, int Nt, int Nx, int Lh, dou
   }
 }
 
-void build_ks_rows(const unsigned* taps, const int* kmin, int nv, int Lh, int Nt,
-                   unsigned short* ks) {
-  const int H = Nt / 2, ldt = taps_row_len(Nt), ldk = ks_row_len(Nt);
+bool build_adj_table(const unsigned* taps, const int* kmin, int nv, int Lh, int Nt, uint2* atab) {
+  const int H = Nt / 2, ldt = taps_row_len(Nt), lda = atab_row_len(Nt);
+  std::vector<int> ks(H + 2);
   for (size_t row = 0; row < (size_t)nv * Lh; ++row) {
-    unsigned short* r = ks + row * ldk;
-    for (int J = 0; J < ldk; ++J) r[J] = 0;
+    uint2* r = atab + row * lda;
+    for (int J = 0; J < lda; ++J) r[J] = make_uint2(0u, 0u);
     const int km = kmin[row];
     if (km >= H) continue;
     const unsigned* t = taps + row * ldt;
     int k = km;
-    for (int J = 0; J <= H; ++J) {
+    for (int J = 0; J <= H + 1; ++J) {
       while (k < H && (int)(t[k] >> 20) < J) ++k;
-      r[J] = (unsigned short)k;
+      ks[J] = k;
+    }
+    for (int J = 0; J <= H; ++J) {
+      const int kB = ks[J], kC = ks[J + 1], kA = J > 0 ? ks[J - 1] : kB;
+      if (kC - kB > 1 || kB - kA > 1) return false;
+      unsigned x = (unsigned)kB << 20, y = 0u;
+      if (kC - kB == 1) {
+        x |= t[kB] & 0xfffffu;
+        y |= 1u << 20;
+      }
+      if (kB - kA == 1) y |= (t[kB - 1] & 0xfffffu) | (1u << 21);
+      r[J] = make_uint2(x, y);
     }
   }
+  return true;
 }
 
 static ashrt_status cuda_fail(cudaError_t e, const char* what) {
@@ -127,8 +139,8 @@ static ashrt_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 static void free_plan_memory(ashrt_plan* p) {
-  void* ptrs[] = {p->tw_t, p->tw_x, p->wt, p->kmin, p->acone, p->taps, p->ks, p->phase, p->X, p->Y,
-                  p->u, p->pv, p->sv, p->wminv, p->r, p->qv, p->wr, p->y,
+  void* ptrs[] = {p->tw_t, p->tw_t16, p->tw_x, p->wt, p->kmin, p->acone, p->taps, p->atab,
+                  p->phase, p->X, p->Y, p->u, p->pv, p->sv, p->wminv, p->r, p->qv, p->wr, p->y,
                   p->scal, p->sel, p->flags, p->cg_coef, p->dev_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -209,6 +221,7 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
   ra.x_batch = ra.x_panel * p->P;
   ra.y_batch = ra.x_panel;
   ra.tw = p->tw_t;
+  ra.tw16 = p->tw_t16;
   ra.wt = p->wt;
   ra.kmin = p->kmin;
   ra.acone = p->acone;
@@ -281,13 +294,14 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
   ra.x_batch = ra.x_panel * p->P;
   ra.y_batch = ra.x_panel;
   ra.tw = p->tw_t;
+  ra.tw16 = p->tw_t16;
   ra.wt = p->wt;
   ra.kmin = p->kmin;
   ra.acone = p->acone;
   ra.taps = p->taps;
   ra.taps_ld = taps_row_len(p->Nt);
-  ra.ks = p->ks;
-  ra.ks_ld = ks_row_len(p->Nt);
+  ra.atab = p->atab;
+  ra.atab_ld = atab_row_len(p->Nt);
   ra.phase = p->shift ? p->phase : nullptr;
   ra.batch = batch;
   ra.minb = p->rows_minb;
@@ -444,8 +458,12 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
   std::vector<float2> acone((size_t)nv * Lh);
   std::vector<unsigned> taps((size_t)nv * Lh * taps_row_len(Nt));
   build_tap_rows(velocities, nv, Nt, Nx, Lh, dt, dx, taps.data(), kmin.data(), acone.data());
-  std::vector<unsigned short> ks((size_t)nv * Lh * ks_row_len(Nt));
-  build_ks_rows(taps.data(), kmin.data(), nv, Lh, Nt, ks.data());
+  std::vector<uint2> atab((size_t)nv * Lh * atab_row_len(Nt));
+  if (!build_adj_table(taps.data(), kmin.data(), nv, Lh, Nt, atab.data())) {
+    set_error("ashrt_plan_create: a bin of the transposed Stolt map has two sources of one kind");
+    delete p;
+    return ASHRT_EINTERNAL;
+  }
   // asymptote shift T: exp(-i w tau0), w = 2 pi kk / (Nt dt)
   std::vector<float2> phase((size_t)nt0 * Nt);
   bool shift = false;
@@ -470,11 +488,17 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
   };
   chk(upload(&p->tw_t, twt, &total));
   chk(upload(&p->tw_x, twx, &total));
+  if (rows16_supported(p->logNt)) {
+    std::vector<float2> tw16(twiddle_table_len(p->logNt, 4));
+    build_twiddle_table(p->logNt, tw16.data(), 4);
+    chk(upload(&p->tw_t16, tw16, &total));
+    p->rows_minb = 4;        // radix-16 forward, radix-8 adjoint: the faster pair
+  }
   chk(upload(&p->wt, wt, &total));
   chk(upload(&p->kmin, kmin, &total));
   chk(upload(&p->acone, acone, &total));
   chk(upload(&p->taps, taps, &total));
-  chk(upload(&p->ks, ks, &total));
+  chk(upload(&p->atab, atab, &total));
   chk(upload(&p->phase, phase, &total));
   const size_t B = (size_t)p->max_batch;
   const size_t xpan = (size_t)Lh * p->ld;

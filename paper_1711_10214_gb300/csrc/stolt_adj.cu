@@ -38,15 +38,15 @@ namespace {
 // Adjoint rows: the exact transpose, in gather form.  The data rows of the
 // gather pair are transformed once and kept in shared memory (weighted by W).
 // For every panel, thread t computes the output bins j = t + T s of the
-// w_tau spectrum.  With J = |j|, bin j receives (1 - f) D(k) from every
-// source k on its side of the spectrum with floor(u(|k|)) = J and f D(k) from
-// every source with floor(u(|k|)) = J - 1 (bin 0 takes the primary taps of
-// both sides).  floor(u) is non-decreasing in |k|, so with ks[J] = the first
-// |k| >= kmin whose floor(u) >= J (a host-built table row, staged with the
-// tap row) the sources of bin J are the run [ks[J-1], ks[J+1]): secondary
-// taps before ks[J], primary taps from it.  Every output bin is written once,
-// by its owner: no atomics, no clearing pass, and the strided ownership
-// spreads the bins outside the cone over all warps.
+// w_tau spectrum.  Bin j receives (1 - f) D(k) from the source k on its side
+// of the spectrum whose tap floor index is |j| (primary) and f D(k) from the
+// one whose floor index is |j| - 1 (secondary); floor(u) is strictly
+// increasing in |k|, so there is at most one of each, and a host-built
+// source table (one 8-byte entry per |j|: both sources' index and fraction,
+// taken from the tap words; see build_adj_table) staged per panel gives them
+// directly.  Every output bin is written once, by its owner: no atomics, no
+// clearing pass, no search, and the strided ownership spreads the bins
+// outside the cone over all warps.
 template <int LOGN, bool SHIFT, int MINB>
 __global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
 stolt_adj_rows(RowArgs a) {
@@ -55,17 +55,13 @@ stolt_adj_rows(RowArgs a) {
   extern __shared__ float4 smem4[];
   float4* buf = smem4;                          // per-panel w_tau spectrum, then its inverse FFT
   float4* dsp = smem4 + N;                      // data spectrum x W (both gathers)
-  unsigned* stap = (unsigned*)(smem4 + 2 * N);  // tap row of the current panel
-  unsigned short* ks = (unsigned short*)(stap + a.taps_ld);   // run starts, [ks_ld]
+  uint2* stab = (uint2*)(smem4 + 2 * N);        // source-table row of the current panel
   const int tid = threadIdx.x, l = blockIdx.x, b0 = 2 * blockIdx.y;
   const bool hasB = b0 + 1 < a.batch;
   const float2* yA = a.Y + (long long)b0 * a.y_batch + (long long)l * a.ld;
-  const unsigned* trow = a.taps + (long long)l * a.taps_ld;
-  const long long tstep = (long long)a.Lh * a.taps_ld;
-  const unsigned short* krow = a.ks + (long long)l * a.ks_ld;
-  const long long kstep = (long long)a.Lh * a.ks_ld;
-  stage_taps(stap, trow, a.taps_ld, tid, T);
-  stage_u16(ks, krow, a.ks_ld, tid, T);
+  const uint2* arow = a.atab + (long long)l * a.atab_ld;
+  const long long astep = (long long)a.Lh * a.atab_ld;
+  stage_tab(stab, arow, a.atab_ld, tid, T);
   cp_async_commit();
 
   float4 v[8];
@@ -84,45 +80,22 @@ stolt_adj_rows(RowArgs a) {
   for (int p = 0; p < a.P; ++p) {
     cp_async_wait_all();
     __syncthreads();
-    const int km = __ldg(a.kmin + iv * a.Lh + l);
+    const bool mapped = __ldg(a.kmin + iv * a.Lh + l) < H;
     const float2* phj = SHIFT ? a.phase + (long long)jt * N : nullptr;
     // the bins this thread gathers, j = tid + T s, are exactly the inputs of
     // its first inverse-FFT butterfly: they stay in registers
     float4 accs[8];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const int j = tid + T * s;
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j != H && km < H) {
-        const bool pos = j < H;
-        const int J = pos ? j : N - j;
-        const int kB = ks[J], kC = ks[J + 1];
-        const int kA = J > 0 ? (int)ks[J - 1] : kB;
-        for (int k = kA; k < kC; ++k) {
-          const float fr = (float)(stap[k] & 0xfffffu) * (1.0f / 1048576.0f);
-          const int kn = pos ? k : N - k;
-          float4 d = dsp[swz4(kn)];
-          if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
-          acc = cfma(k < kB ? fr : 1.f - fr, d, acc);
-        }
-        if (j == 0) {                            // bin 0 also takes the primary taps of -k
-          for (int k = kB; k < kC; ++k) {
-            const float fr = (float)(stap[k] & 0xfffffu) * (1.0f / 1048576.0f);
-            float4 d = dsp[swz4(N - k)];
-            if (SHIFT) d = cmul(d, cconj(__ldg(phj + (N - k))));
-            acc = cfma(1.f - fr, d, acc);
-          }
-        }
-      }
-      accs[s] = acc;
-    }
+    for (int s = 0; s < 8; ++s)
+      accs[s] = mapped ? adj_gather_bin<N, 3, SHIFT>(dsp, stab, tid + T * s, phj)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid == 0 && mapped) accs[0] = adj_gather_bin0_mirror<N, 3, SHIFT>(dsp, stab, phj, accs[0]);
     // first pass from the registers (its barrier also ends every thread's
-    // reads of the tap and run-start rows, which are then restaged)
+    // reads of the source-table row, which is then restaged)
     row_first_pass<+1, N>(buf, accs, tid);
     if (p + 1 < a.P) {
       const int ivn = iv + 1 == a.nv ? 0 : iv + 1;
-      stage_taps(stap, trow + ivn * tstep, a.taps_ld, tid, T);
-      stage_u16(ks, krow + ivn * kstep, a.ks_ld, tid, T);
+      stage_tab(stab, arow + ivn * astep, a.atab_ld, tid, T);
       cp_async_commit();
     }
     row_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw, tid);
@@ -140,8 +113,7 @@ template <int LOGN, bool SHIFT, int MINB>
 cudaError_t launch_adj_v(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
-  const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.taps_ld * sizeof(unsigned) +
-                      (size_t)a.ks_ld * sizeof(unsigned short);
+  const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.atab_ld * sizeof(uint2);
   cudaError_t e = set_smem(stolt_adj_rows<LOGN, SHIFT, MINB>, smem_cap<LOGN>(false), attr);
   if (e != cudaSuccess) return e;
   stolt_adj_rows<LOGN, SHIFT, MINB><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
@@ -171,15 +143,21 @@ cudaError_t launch_adj_t(const RowArgs& a, cudaStream_t s) {
 
 }  // namespace
 
+// Variants (a.minb): 1..3 radix-8 with that register cap; 4 radix-8 cap 3
+// (the forward alone is radix-16); 5 the radix-16 adjoint (stolt_r16.cu)
+// where its twiddles exist, else cap 3.
 cudaError_t launch_stolt_adj_rows(const RowArgs& a, cudaStream_t s) {
-  switch (row_log2(a.Nt)) {
-    case 6: return launch_adj_t<6>(a, s);
-    case 7: return launch_adj_t<7>(a, s);
-    case 8: return launch_adj_t<8>(a, s);
-    case 9: return launch_adj_t<9>(a, s);
-    case 10: return launch_adj_t<10>(a, s);
-    case 11: return launch_adj_t<11>(a, s);
-    case 12: return launch_adj_t<12>(a, s);
+  if (a.minb == 5 && a.tw16) return launch_stolt_adj_rows16(a, s);
+  RowArgs b = a;
+  if (b.minb > 3) b.minb = 3;
+  switch (row_log2(b.Nt)) {
+    case 6: return launch_adj_t<6>(b, s);
+    case 7: return launch_adj_t<7>(b, s);
+    case 8: return launch_adj_t<8>(b, s);
+    case 9: return launch_adj_t<9>(b, s);
+    case 10: return launch_adj_t<10>(b, s);
+    case 11: return launch_adj_t<11>(b, s);
+    case 12: return launch_adj_t<12>(b, s);
     default: return cudaErrorInvalidValue;
   }
 }

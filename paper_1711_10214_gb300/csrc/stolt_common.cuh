@@ -94,9 +94,60 @@ __device__ __forceinline__ void stage_taps(unsigned* dst, const unsigned* src, i
   for (int c = tid; c < (taps_ld >> 2); c += T) cp_async16(dst + 4 * c, src + 4 * c);
 }
 
-__device__ __forceinline__ void stage_u16(unsigned short* dst, const unsigned short* src, int n,
-                                          int tid, int T) {
-  for (int c = tid; c < (n >> 3); c += T) cp_async16(dst + 8 * c, src + 8 * c);
+// Stage one adjoint source-table row (n entries, n even; 16-byte aligned).
+__device__ __forceinline__ void stage_tab(uint2* dst, const uint2* src, int n, int tid, int T) {
+  for (int c = tid; c < (n >> 1); c += T) cp_async16(dst + 2 * c, src + 2 * c);
+}
+
+// Swizzle of a shared float4 row: XOR the 16-byte bank group (low 3 bits)
+// with bits SW..SW+2 of the index (SW = 3: swz4 of common.cuh).
+template <int SW>
+__device__ __forceinline__ int swz_g(int i) {
+  return i ^ ((i >> SW) & 7);
+}
+
+// One output bin j of the transposed Stolt map, gather form: the secondary
+// source kB - 1 (weight f(kB - 1)) and the primary source kB (weight
+// 1 - f(kB)) of |j| from the staged source-table row (see build_adj_table),
+// on j's side of the spectrum; the w-Nyquist bin takes nothing.  dsp holds
+// the weighted data spectrum; with SHIFT each source is multiplied by the
+// conjugate asymptote phase of its own bin.
+template <int N, int SW, bool SHIFT>
+__device__ __forceinline__ float4 adj_gather_bin(const float4* dsp, const uint2* stab, int j,
+                                                 const float2* __restrict__ phj) {
+  constexpr int H = N / 2;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (j == H) return acc;
+  const bool pos = j < H;
+  const uint2 e = stab[pos ? j : N - j];
+  const int kB = (int)(e.x >> 20);
+  if (e.y & (1u << 21)) {
+    const int kn = pos ? kB - 1 : N - kB + 1;
+    float4 d = dsp[swz_g<SW>(kn)];
+    if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
+    acc = cscale(d, (float)(e.y & 0xfffffu) * (1.0f / 1048576.0f));
+  }
+  if (e.y & (1u << 20)) {
+    const int kn = pos ? kB : N - kB;
+    float4 d = dsp[swz_g<SW>(kn)];
+    if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
+    acc = cfma(1.f - (float)(e.x & 0xfffffu) * (1.0f / 1048576.0f), d, acc);
+  }
+  return acc;
+}
+
+// Bin 0 also takes the primary tap of -kB (w = 0 lies on both sides).
+template <int N, int SW, bool SHIFT>
+__device__ __forceinline__ float4 adj_gather_bin0_mirror(const float4* dsp, const uint2* stab,
+                                                         const float2* __restrict__ phj, float4 acc) {
+  const uint2 e = stab[0];
+  if (e.y & (1u << 20)) {
+    const int kn = N - (int)(e.x >> 20);
+    float4 d = dsp[swz_g<SW>(kn)];
+    if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
+    acc = cfma(1.f - (float)(e.x & 0xfffffu) * (1.0f / 1048576.0f), d, acc);
+  }
+  return acc;
 }
 
 template <int N>
@@ -121,17 +172,18 @@ inline cudaError_t set_smem(K kern, size_t bytes, bool& done) {
   return e;
 }
 
-// Shared bytes of the adjoint's run-start row (ks_row_len u16)
-inline constexpr size_t adj_ks_bytes(int N) { return (size_t)(((N / 2 + 2) + 7) & ~7) * 2; }
+// Shared bytes of the adjoint's source-table row (atab_row_len entries)
+inline constexpr size_t adj_tab_bytes(int N) { return (size_t)(((N / 2 + 1) + 1) & ~1) * 8; }
 
 // Largest dynamic shared memory a launch of the LOGN kernels may request
-// (ld <= Nt, taps row <= Nt/2 + 4 words): the attribute is set once to it.
+// (ld <= Nt, taps row <= Nt/2 + 4 words, source-table row Nt/2 + 2
+// entries): the attribute is set once to it.
 template <int LOGN>
 inline size_t smem_cap(bool fwd) {
   constexpr int N = 1 << LOGN;
   const size_t taps = (size_t)(N / 2 + 4) * sizeof(unsigned);
   return fwd ? (size_t)N * sizeof(float4) + (size_t)2 * N * sizeof(float2) + 2 * taps
-             : (size_t)2 * N * sizeof(float4) + taps + adj_ks_bytes(N);
+             : (size_t)2 * N * sizeof(float4) + adj_tab_bytes(N);
 }
 
 inline int row_log2(int n) {

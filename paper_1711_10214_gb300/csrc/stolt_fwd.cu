@@ -156,15 +156,20 @@ cudaError_t launch_fwd_t(const RowArgs& a, cudaStream_t s) {
 
 }  // namespace
 
+// Variants (a.minb): 1..3 radix-8 with that register cap; 4 and 5 use the
+// radix-16 forward (stolt_r16.cu) where its twiddles exist, else cap 3.
 cudaError_t launch_stolt_fwd_rows(const RowArgs& a, cudaStream_t s) {
-  switch (row_log2(a.Nt)) {
-    case 6: return launch_fwd_t<6>(a, s);
-    case 7: return launch_fwd_t<7>(a, s);
-    case 8: return launch_fwd_t<8>(a, s);
-    case 9: return launch_fwd_t<9>(a, s);
-    case 10: return launch_fwd_t<10>(a, s);
-    case 11: return launch_fwd_t<11>(a, s);
-    case 12: return launch_fwd_t<12>(a, s);
+  if (a.minb >= 4 && a.tw16) return launch_stolt_fwd_rows16(a, s);
+  RowArgs b = a;
+  if (b.minb > 3) b.minb = 3;
+  switch (row_log2(b.Nt)) {
+    case 6: return launch_fwd_t<6>(b, s);
+    case 7: return launch_fwd_t<7>(b, s);
+    case 8: return launch_fwd_t<8>(b, s);
+    case 9: return launch_fwd_t<9>(b, s);
+    case 10: return launch_fwd_t<10>(b, s);
+    case 11: return launch_fwd_t<11>(b, s);
+    case 12: return launch_fwd_t<12>(b, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -29,7 +29,7 @@ def test_every_variant_matches_oracle(lib):
     ref_m = stolt.adjoint_batch(g, d)
     dev = torch.device("cuda:0")
     md, dd = torch.from_numpy(m).to(dev), torch.from_numpy(d).to(dev)
-    for minb in (1, 2, 3):
+    for minb in (1, 2, 3, 4, 5):
         for cols in (8, 16):
             plan.set_variant(minb, cols)
             od, om = torch.empty_like(dd), torch.empty_like(md)
@@ -46,7 +46,7 @@ def test_autotune_choice_and_cache(lib, tmp_path):
     plan = ashrt.Plan(300, 100, DT, DX, [1500.0, 2600.0], max_batch=4)
     cache = str(tmp_path / "tune.jsonl")
     mb, cols = plan.autotune(batch=4, cache_path=cache)
-    assert mb in (1, 2, 3) and cols in (8, 16)
+    assert mb in (1, 2, 3, 4, 5) and cols in (8, 16)
     lines = [json.loads(x) for x in open(cache)]
     assert len(lines) == 1 and lines[0]["rows_minb"] == mb and lines[0]["xfft_cols"] == cols
     plan2 = ashrt.Plan(300, 100, DT, DX, [1500.0, 2600.0], max_batch=4)
@@ -54,3 +54,45 @@ def test_autotune_choice_and_cache(lib, tmp_path):
     assert len(open(cache).readlines()) == 1           # served from the cache
     plan.close()
     plan2.close()
+
+
+@pytest.mark.parametrize("nt,nx,v,t0,batch,mask,kw", [
+    (600, 48, [1700.0, 2600.0], None, 3, False, {}),                          # Nt 2048: 16 x 16 x 8
+    (1500, 20, [2100.0], None, 2, True, {}),                                   # Nt 4096: 16 x 16 x 16
+    (400, 30, [1500.0, 2300.0], [0.0, 0.05], 2, False,
+     dict(wavelet_peak_hz=25.0, fmax_hz=90.0)),                               # Nt 1024, AASHRT + C
+    (1024, 17, [0.0, 2500.0], None, 1, False, dict(pad_t=4)),                 # Nt 4096, v = 0, pad 4
+])
+def test_radix16_rows_match_oracle(lib, nt, nx, v, t0, batch, mask, kw):
+    """The radix-16 row kernels (variant 5: both directions) on every length
+    they serve, with the asymptote shift, the sampling mask and an odd batch
+    (a lone gather in the last pair)."""
+    import torch
+    from paper_1711_10214_gb300 import ashrt
+    plan = ashrt.Plan(nt, nx, DT, DX, v, t0s=t0, max_batch=batch, **kw)
+    plan.set_variant(5, 16)
+    g = stolt.Geometry(nt, nx, DT, DX, v, t0s=(0.0,) if t0 is None else t0, **kw)
+    rng = np.random.default_rng(77)
+    m = rng.standard_normal((batch,) + g.model_shape).astype(np.float32)
+    d = rng.standard_normal((batch,) + g.data_shape).astype(np.float32)
+    mk = (rng.random((batch, nx)) < 0.6).astype(np.float32) if mask else None
+    dev = torch.device("cuda:0")
+    md, dd = torch.from_numpy(m).to(dev), torch.from_numpy(d).to(dev)
+    mkd = torch.from_numpy(mk).to(dev) if mask else None
+    od, om = torch.empty_like(dd), torch.empty_like(md)
+    plan.forward(md, od, mask=mkd, batch=batch)
+    plan.adjoint(dd, om, mask=mkd, batch=batch)
+    torch.cuda.synchronize()
+    assert _rel(od.cpu().numpy(), stolt.forward_batch(g, m, mk)) <= 1e-4
+    assert _rel(om.cpu().numpy(), stolt.adjoint_batch(g, d, mk)) <= 1e-4
+    plan.close()
+
+
+def test_radix16_rejected_where_it_does_not_apply(lib):
+    from paper_1711_10214_gb300 import ashrt
+    plan = ashrt.Plan(100, 20, DT, DX, [2000.0])        # Nt 256
+    with pytest.raises(ashrt.AshrtError):
+        plan.set_variant(4, 16)
+    with pytest.raises(ashrt.AshrtError):
+        plan.set_variant(5, 16)
+    plan.close()
