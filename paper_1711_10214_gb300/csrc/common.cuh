@@ -147,6 +147,15 @@ __device__ __forceinline__ void twiddle_r(E* v, float2 w) {
   }
 }
 
+// 16-byte asynchronous global -> shared copies (Ampere-style cp.async; no
+// waits beyond cp.async.wait_group, which the hardware completes).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
 // Radix schedule of a length 2^LOGN transform.
 template <int LOGN>
 struct Sched {

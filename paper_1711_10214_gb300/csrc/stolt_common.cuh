@@ -69,15 +69,6 @@ __device__ __forceinline__ int kabs_of(int k) {
   return k <= N / 2 ? k : N - k;
 }
 
-// 16-byte asynchronous global -> shared copies (Ampere-style cp.async; no
-// waits beyond cp.async.wait_group, which the hardware completes).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
 // Stage the rows of gathers A and B (B may be absent) of one panel: ld
 // complex values each (ld is a multiple of 4, rows are 32-byte aligned).
 __device__ __forceinline__ void stage_rows(float2* stage, const float2* rowA, const float2* rowB,

@@ -372,17 +372,33 @@ __device__ __forceinline__ float4 herm_load2(const float2* __restrict__ base, in
   return make_float4(ok ? y.x : 0.f, ok ? y.y * sy : 0.f, okb ? y.z : 0.f, okb ? y.w * sy : 0.f);
 }
 
-template <int LOGN, int C>
+// PF: the tile of the elementwise weight ew that this CTA's outputs use
+// ([nx][2C] floats) is copied into shared memory with cp.async when the CTA
+// starts, so the epilogue reads it from there instead of waiting on global
+// loads after the transform (host condition: nt a multiple of 4, the tile
+// fits; 16-byte chunks wholly inside the row are copied, the rest are never
+// read).
+template <int LOGN, int C, bool PF>
 __global__ void __launch_bounds__((1 << LOGN) * C / 16)
 xfft_c2r_kernel(XfftArgs a) {
   constexpr int N = 1 << LOGN, T = N * C / 16, JS = T / C;
   using S = Sched<LOGN>;
-  extern __shared__ float2 sm[];   // [N][C]
+  extern __shared__ float2 sm[];   // [N][C], then (PF) the weight tile [nx][2C] floats
   const int tid = threadIdx.x, col = tid % C, j0 = tid / C;
   const long long slab = blockIdx.x;
   const int t0 = blockIdx.y * 2 * C;
   const int ta = t0 + 2 * col;
   const float2* in = a.in_cplx + slab * a.slab_cplx;
+  float* sew = (float*)(sm + N * C);
+  if (PF) {
+    const float* ews = a.ew + slab * a.slab_real;
+    constexpr int CPR = C / 2;                   // 16-byte chunks per tile row
+    for (int c = tid; c < a.nx * CPR; c += T) {
+      const int row = c / CPR, q = c % CPR, t = t0 + 4 * q;
+      if (t < a.nt) cp_async16(sew + row * 2 * C + 4 * q, ews + (long long)row * a.nt + t);
+    }
+    cp_async_commit();
+  }
 
   // first pass: Z = A + i B, A and B the Hermitian-extended spectra of columns ta, ta + 1
   float2 v[2][8];
@@ -404,6 +420,10 @@ xfft_c2r_kernel(XfftArgs a) {
   }
   __syncthreads();
   col_pass_range<+1, LOGN, C, 1, S::NPASS - 1>(sm, a.tw, tid);
+  if (PF) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
 
   // last pass straight to global: output r of butterfly jb is trace jb + r Ns;
   // real part -> column ta, imaginary part -> column ta + 1
@@ -433,17 +453,19 @@ xfft_c2r_kernel(XfftArgs a) {
         float2 x = w[q * R + r];
         const float g = tm ? __ldg(tm + row) : 1.f;
         if (vec && ta + 1 < a.nt) {
-          float2 e = ew ? __ldg((const float2*)(ew + o)) : make_float2(1.f, 1.f);
+          float2 e = PF ? *(const float2*)(sew + row * 2 * C + 2 * col)
+                        : (ew ? __ldg((const float2*)(ew + o)) : make_float2(1.f, 1.f));
           x.x *= g * e.x;
           x.y *= g * e.y;
           *(float2*)(out + o) = x;
           ss = fmaf(x.x, x.x, fmaf(x.y, x.y, ss));
         } else {
-          const float xa = x.x * g * (ew ? __ldg(ew + o) : 1.f);
+          const float xa = x.x * g * (PF ? sew[row * 2 * C + 2 * col] : (ew ? __ldg(ew + o) : 1.f));
           out[o] = xa;
           ss = fmaf(xa, xa, ss);
           if (ta + 1 < a.nt) {
-            const float xb = x.y * g * (ew ? __ldg(ew + o + 1) : 1.f);
+            const float xb =
+                x.y * g * (PF ? sew[row * 2 * C + 2 * col + 1] : (ew ? __ldg(ew + o + 1) : 1.f));
             out[o + 1] = xb;
             ss = fmaf(xb, xb, ss);
           }
@@ -508,20 +530,32 @@ cudaError_t launch_r2c_tma(const XfftArgs& a, cudaStream_t s, bool* used) {
   return cudaGetLastError();
 }
 
-template <int LOGN, int C>
-cudaError_t launch_c2r_v(const XfftArgs& a, cudaStream_t s) {
+template <int LOGN, int C, bool PF>
+cudaError_t launch_c2r_pf(const XfftArgs& a, cudaStream_t s, size_t smem) {
   constexpr int N = 1 << LOGN, T = N * C / 16;
-  const size_t smem = (size_t)N * C * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(xfft_c2r_kernel<LOGN, C>,
+  static size_t attr = 0;
+  if (smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(xfft_c2r_kernel<LOGN, C, PF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr = smem;
   }
   dim3 grid(a.slabs, (a.nt + 2 * C - 1) / (2 * C));
-  xfft_c2r_kernel<LOGN, C><<<grid, T, smem, s>>>(a);
+  xfft_c2r_kernel<LOGN, C, PF><<<grid, T, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// The weight tile goes through shared memory when there is a weight, its
+// rows are 16-byte aligned (nt a multiple of 4) and the CTA's shared memory
+// stays within 160 KB (two CTAs per SM).
+template <int LOGN, int C>
+cudaError_t launch_c2r_v(const XfftArgs& a, cudaStream_t s) {
+  constexpr int N = 1 << LOGN;
+  const size_t base = (size_t)N * C * sizeof(float2);
+  const size_t tile = (size_t)a.nx * 2 * C * sizeof(float);
+  if (a.ew && (a.nt & 3) == 0 && base + tile <= 160 * 1024)
+    return launch_c2r_pf<LOGN, C, true>(a, s, base + tile);
+  return launch_c2r_pf<LOGN, C, false>(a, s, base);
 }
 
 // Column-tile variant: 16 complex columns per CTA (autotuner default) or 8;
