@@ -292,9 +292,9 @@ def run_ours(args):
     achieved = flops / per_launch_s / 1e12
     # DRAM bytes per launch of the dominant kernel, from one ncu capture of the
     # 8-gather launch of the same kernel (dram__bytes_read.sum +
-    # dram__bytes_write.sum = 672.2 MB for the radix-8 adjoint with its source
+    # dram__bytes_write.sum = 672.5 MB for the radix-8 adjoint with its source
     # table), scaled by the gathers per launch
-    traffic = {"stolt_adj_rows": 672.2e6 / 8}.get(dom)
+    traffic = {"stolt_adj_rows": 672.5e6 / 8}.get(dom)
     traffic = traffic * B if traffic is not None else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
