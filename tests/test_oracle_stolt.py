@@ -3,7 +3,9 @@
 Each pin checks the oracle against something other than itself: the
 transpose identity, closed-form special cases (v = 0, laterally constant
 models, integer-sample asymptote shifts), exact linear-interpolation values,
-and the analytic traveltime curve of ch. 3 Table ch3_table_Radon_operators.
+the slope bound of the dispersion relation (at most one source of each kind
+per output bin), and the analytic traveltime curve of ch. 3 Table
+ch3_table_Radon_operators.
 """
 import numpy as np
 import pytest
@@ -121,6 +123,39 @@ def test_map_is_exact_linear_interpolation_of_u():
                 assert abs(V[l, idx] - (alpha + beta * u)) < 1e-9, (l, k)
             else:
                 assert V[l, idx] == 0.0
+
+
+@pytest.mark.parametrize("nt,nx,v", [
+    (1024, 256, synth.velocity_scan(1400.0, 3500.0, 32)),     # the benchmark geometry
+    (64, 16, [0.0, 900.0, 1700.0, 5000.0]),
+    (300, 37, [1234.5, 2999.0]),
+])
+def test_each_bin_has_at_most_one_source_of_each_kind(nt, nx, v):
+    """u(k + 1) - u(k) = (2k + 1) / (u(k + 1) + u(k)) >= 1 because u(k) <= k:
+    on each side of the spectrum the floor tap of consecutive mapped bins
+    strictly increases, so every output bin receives at most one primary
+    (weight 1 - f) and one secondary (weight f) contribution.  The GPU
+    adjoint's source table depends on this; here it is checked on the
+    oracle's own FP64 taps, row by row."""
+    g = stolt.Geometry(nt, nx, DT, DX, v)
+    H = g.Nt // 2
+    kk = np.arange(g.Nt)
+    kk = np.where(kk <= H, kk, kk - g.Nt)
+    for iv in range(len(v)):
+        rows, i0, i1, w0, w1, incone = g._taps[iv]
+        u = np.where(incone, np.sign(kk) * np.sqrt(np.maximum(
+            kk.astype(float) ** 2 - g.cone_a(float(g.v[iv]))[:, None] ** 2, 0.0)), 0.0)
+        for l in range(g.Nx):
+            for side in (kk > 0, kk < 0):
+                sel = incone[l] & side
+                if not sel.any():
+                    continue
+                uu = np.abs(u[l][sel])
+                order = np.argsort(np.abs(kk[sel]))
+                assert np.all(np.diff(uu[order]) >= 1.0 - 1e-12), (iv, l)
+                assert np.all(np.diff(np.floor(uu[order])) >= 1), (iv, l)
+                assert len(np.unique(i0[l][sel])) == sel.sum()
+                assert len(np.unique(i1[l][sel])) == sel.sum()
 
 
 def _win_peak(d, tc, w):
