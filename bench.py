@@ -41,9 +41,10 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="deblend", choices=["deblend", "ops", "unet"],
+    ap.add_argument("--mode", default="deblend", choices=["deblend", "ops", "unet", "td"],
                     help="ops: forward+adjoint operator pairs only; unet: warm-start U-Net "
-                         "inference (profiling aids)")
+                         "inference; td: time-domain (hyperbolic summation) pair against the "
+                         "Stolt pair on the same gathers (profiling aids)")
     ap.add_argument("--batch", type=int, default=B,
                     help="gathers per call (the deblend workload is 64; smaller batches are "
                          "for profiling captures)")
@@ -398,8 +399,53 @@ def run_unet(args):
     net.close()
 
 
+def run_td(args):
+    """The thesis's ch. 5 speed comparison on one GPU: time-domain ASHRT
+    (hyperbolic summation) against the Stolt form, forward + adjoint pairs on
+    the same gathers (not the bench line)."""
+    import torch
+
+    from paper_1711_10214_gb300 import ashrt, synth
+    dev = torch.device("cuda", 0)
+    nb = args.batch
+    v = synth.velocity_scan(1400.0, 3500.0, NV)
+    plan = ashrt.Plan(NT, NX, DT, DX, v, max_batch=nb)
+    g = torch.Generator(device=dev).manual_seed(0)
+    m = torch.randn((nb,) + plan.model_shape, device=dev, generator=g)
+    d = torch.randn((nb, NX, NT), device=dev, generator=g)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms = {
+        "td_forward": timed(lambda: ashrt.td_forward(NT, NX, DT, DX, v, m, d, batch=nb)),
+        "td_adjoint": timed(lambda: ashrt.td_adjoint(NT, NX, DT, DX, v, d, m, batch=nb)),
+        "stolt_forward": timed(lambda: plan.forward(m, d, batch=nb)),
+        "stolt_adjoint": timed(lambda: plan.adjoint(d, m, batch=nb)),
+    }
+    td = ms["td_forward"] + ms["td_adjoint"]
+    st = ms["stolt_forward"] + ms["stolt_adjoint"]
+    print(json.dumps({"mode": "td", "batch": nb, "nt": NT, "nx": NX, "nv": NV,
+                      "ms_per_call": ms, "td_pairs_per_s": nb * 1000.0 / td,
+                      "stolt_pairs_per_s": nb * 1000.0 / st, "stolt_speedup": td / st}),
+          flush=True)
+    plan.close()
+
+
 def main():
     args = _args()
+    if args.mode == "td":
+        run_td(args)
+        return
     if args.mode == "ops":
         run_ops(args)
         return

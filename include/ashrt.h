@@ -147,6 +147,35 @@ ashrt_status ashrt_forward_static(int nt, int nx, double dt, double dx,
                                   const ashrt_opts* opts, const float* m_dev, float* d_dev,
                                   const float* trace_mask_dev, int batch, void* stream);
 
+/*
+ * Time-domain ASHRT / AASHRT by hyperbolic summation: the classical form of
+ * the operator pair (ch. 3 Table ch3_table_Radon_operators, ASHRT row; ch. 6
+ * Eq. ch6_AASHRT_adjoint) that ch. 5 compares the Stolt form against, with
+ * cost O(nx^2 nt nv nt0) per gather.  The adjoint sums each trace x_r along
+ * the hyperbola t = tau0 + sqrt(tau^2 + (x_r - x_a)^2 / v^2) of every
+ * (tau, v, x_a, tau0), reading d at the fractional time by linear
+ * interpolation between samples (a sample at or past nt reads 0); the
+ * forward is its exact transpose.  No padding, no wavelet, no band limit:
+ * this is a different discretisation of the operator than the Stolt pair,
+ * not a copy of it.
+ *   nt (2..4096), nx (>= 1), dt, dx (> 0)   gather sampling
+ *   velocities   host array of nv scan velocities [m/s], each > 0
+ *   t0_shifts    host array of nt0 asymptote shifts [s], each >= 0, or NULL
+ *                with nt0 = 1 (ASHRT); nv * nt0 <= 256
+ *   m_dev        [batch][nt0][nv][nx][nt] model (read by forward, written by adjoint)
+ *   d_dev        [batch][nx][nt] data (written by forward, read by adjoint)
+ * Asynchronous on `stream`, one kernel launch, no allocation, no plan.  The
+ * forward accumulates with shared-memory atomic adds, so its last bits
+ * depend on scheduling.  Argument errors return ASHRT_EINVAL before any
+ * CUDA call.
+ */
+ashrt_status ashrt_td_forward(int nt, int nx, double dt, double dx, const float* velocities,
+                              int nv, const float* t0_shifts, int nt0, const float* m_dev,
+                              float* d_dev, int batch, void* stream);
+ashrt_status ashrt_td_adjoint(int nt, int nx, double dt, double dx, const float* velocities,
+                              int nv, const float* t0_shifts, int nt0, const float* d_dev,
+                              float* m_dev, int batch, void* stream);
+
 /* Options of the robust solve (ch. 4). */
 typedef struct {
   double p;               /* misfit norm exponent, 0 < p <= 2 (1 = robust) */

@@ -83,6 +83,10 @@ def load():
                                          P(c_float), c_int, P(AshrtOpts), c_void_p, c_void_p,
                                          c_void_p, c_int, c_void_p]
     lib.ashrt_forward_static.restype = c_int
+    for f in (lib.ashrt_td_forward, lib.ashrt_td_adjoint):
+        f.argtypes = [c_int, c_int, c_double, c_double, P(c_float), c_int, P(c_float), c_int,
+                      c_void_p, c_void_p, c_int, c_void_p]
+        f.restype = c_int
     lib.ashrt_batch_create.argtypes = [P(c_void_p), c_int, P(c_int), c_int, c_double, c_double,
                                        P(c_float), c_int, P(c_float), c_int, P(AshrtOpts)]
     lib.ashrt_batch_create.restype = c_int
@@ -212,6 +216,27 @@ def forward_static(nt, nx, dt, dx, velocities, m, d, t0s=None, mask=None, batch=
     _check(lib.ashrt_forward_static(int(nt), int(nx), float(dt), float(dx), vp, va.size, tp,
                                     nt0, ctypes.byref(o), _ptr(m), _ptr(d), _ptr(mask),
                                     int(batch), _stream(stream)))
+
+
+def _td(fn, nt, nx, dt, dx, velocities, src, dst, t0s, batch, stream):
+    va, vp = _farr(velocities)
+    if t0s is None:
+        tp, nt0 = None, 1
+    else:
+        ta, tp = _farr(t0s)
+        nt0 = ta.size
+    _check(fn(int(nt), int(nx), float(dt), float(dx), vp, va.size, tp, nt0, _ptr(src), _ptr(dst),
+              int(batch), _stream(stream)))
+
+
+def td_forward(nt, nx, dt, dx, velocities, m, d, t0s=None, batch=1, stream=None):
+    """ashrt_td_forward: time-domain (hyperbolic summation) forward, m -> d."""
+    _td(load().ashrt_td_forward, nt, nx, dt, dx, velocities, m, d, t0s, batch, stream)
+
+
+def td_adjoint(nt, nx, dt, dx, velocities, d, m, t0s=None, batch=1, stream=None):
+    """ashrt_td_adjoint: time-domain (hyperbolic summation) adjoint, d -> m."""
+    _td(load().ashrt_td_adjoint, nt, nx, dt, dx, velocities, d, m, t0s, batch, stream)
 
 
 class Plan:

@@ -56,3 +56,24 @@ def test_host_side_calls_without_gpu(cdll):
     ax = (ctypes.c_float * 3)(0.0, 12.5, 30.0)     # apex grid must equal the trace grid
     st = cdll.ashrt_plan_create(ctypes.byref(h), 64, 3, 0.004, 12.5, v, 1, ax, 3, None, 1, None)
     assert st == 1 and b"x_a must equal x" in cdll.ashrt_last_error()
+
+
+def test_time_domain_argument_checks_without_gpu(cdll):
+    """ashrt_td_forward / ashrt_td_adjoint reject bad arguments before any CUDA
+    call (the pointers are never dereferenced on these paths)."""
+    v = (ctypes.c_float * 2)(1500.0, 2500.0)
+    bad_v = (ctypes.c_float * 2)(1500.0, -1.0)
+    t0 = (ctypes.c_float * 1)(-0.1,)
+    buf = ctypes.c_void_p(16)                      # never dereferenced
+    for fn in (cdll.ashrt_td_forward, cdll.ashrt_td_adjoint):
+        fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        assert fn(1, 8, 0.004, 12.5, v, 2, None, 1, buf, buf, 1, None) == 1
+        assert fn(64, 8, 0.004, 12.5, bad_v, 2, None, 1, buf, buf, 1, None) == 1
+        assert b"velocity 1" in cdll.ashrt_last_error()
+        assert fn(64, 8, 0.004, 12.5, v, 2, t0, 1, buf, buf, 1, None) == 1
+        assert b"shift 0" in cdll.ashrt_last_error()
+        assert fn(64, 8, 0.004, 12.5, v, 2, None, 200, buf, buf, 1, None) == 1
+        assert fn(64, 8, 0.004, 12.5, v, 2, None, 1, None, buf, 1, None) == 1
+        assert fn(64, 8, -0.004, 12.5, v, 2, None, 1, buf, buf, 1, None) == 1
