@@ -41,10 +41,11 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="deblend", choices=["deblend", "ops", "unet", "td"],
+    ap.add_argument("--mode", default="deblend", choices=["deblend", "ops", "unet", "td", "fista"],
                     help="ops: forward+adjoint operator pairs only; unet: warm-start U-Net "
                          "inference; td: time-domain (hyperbolic summation) pair against the "
-                         "Stolt pair on the same gathers (profiling aids)")
+                         "Stolt pair on the same gathers; fista: l2-l1 interpolation by FISTA "
+                         "on the gathers with 4 of 5 traces removed (profiling aids)")
     ap.add_argument("--batch", type=int, default=B,
                     help="gathers per call (the deblend workload is 64; smaller batches are "
                          "for profiling captures)")
@@ -441,8 +442,50 @@ def run_td(args):
     plan.close()
 
 
+def run_fista(args):
+    """FISTA interpolation (ch. 6 "Sparse inversion") on the workload's
+    gathers with one trace in five kept: 20 power-method and 30 FISTA
+    iterations per call (not the bench line)."""
+    import torch
+
+    from paper_1711_10214_gb300 import ashrt, synth
+    dev = torch.device("cuda", 0)
+    nb = args.batch
+    c = synth.config2(nb, NT, NX, NV)
+    d = torch.from_numpy(c["blended"].astype("float32")).to(dev)
+    plan = ashrt.Plan(NT, NX, DT, DX, c["velocities"], wavelet_peak_hz=F_PEAK, max_batch=nb,
+                      with_solver=True)
+    mask = torch.zeros((nb, NX), device=dev)
+    mask[:, ::5] = 1.0
+    g = torch.Generator(device=dev).manual_seed(0)
+    v0 = torch.randn((nb,) + plan.model_shape, device=dev, generator=g)
+    m = torch.empty((nb,) + plan.model_shape, device=dev)
+    drec = torch.empty_like(d)
+    n_iter, n_power = 30, 20
+    for _ in range(args.warmup):
+        plan.fista(d, m, v0, drec=drec, mask=mask, batch=nb, mu=0.01, n_iter=n_iter,
+                   n_power=n_power)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.fista(d, m, v0, drec=drec, mask=mask, batch=nb, mu=0.01, n_iter=n_iter,
+                   n_power=n_power)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    pairs = n_iter + n_power + 1.0 / 2.0          # + the reconstruction forward
+    print(json.dumps({"mode": "fista", "batch": nb, "n_iter": n_iter, "n_power": n_power,
+                      "ms_per_call": ms, "gathers_per_s": nb * 1000.0 / ms,
+                      "pairs_per_s": nb * pairs * 1000.0 / ms}), flush=True)
+    plan.close()
+
+
 def main():
     args = _args()
+    if args.mode == "fista":
+        run_fista(args)
+        return
     if args.mode == "td":
         run_td(args)
         return

@@ -241,6 +241,36 @@ ashrt_status robust_irls_deblend(const ashrt_plan* plan, const float* d_dev, flo
                                  irls_report* per_gather, void* stream);
 
 /*
+ * Sparse inversion by FISTA for AASHRT interpolation (ch. 6, "Sparse
+ * inversion": Eq. cost_fn with p = 2, q = 1):
+ *   minimise J(m) = ||S (d - L m)||_2^2 + mu ||m||_1
+ * with L the plan's forward and S the trace mask, by the fast iterative
+ * shrinkage-thresholding algorithm (Beck and Teboulle 2009) with step 1/Lf,
+ * Lf = 2 lambda_max(L^T S^T S L) from n_power iterations of Rayleigh's power
+ * method started at v0 (the caller's random draw, normalised here).  The model
+ * starts at zero; every gather runs n_iter iterations with its own Lf.
+ *   d_dev           [batch][nx][nt] data (read; traces with mask 0 are ignored)
+ *   trace_mask_dev  [batch][nx] sampling weights S, or NULL (all traces)
+ *   v0_dev          [batch][nt0][nv][nx][nt] power-method start (read)
+ *   m_dev           [batch][nt0][nv][nx][nt] the sparse model (written)
+ *   drec_dev        [batch][nx][nt] L m on every trace -- the interpolated
+ *                   gather -- or NULL
+ *   lipschitz       host array of batch Lf values (written), or NULL
+ * Requires a plan created with with_solver = 1 (its solver vectors are the
+ * workspace).  Asynchronous on `stream` until one synchronisation at the end.
+ * lambda = 0 (nothing sampled) leaves that gather's model at zero.
+ */
+typedef struct {
+  double mu;              /* trade-off of Eq. cost_fn, >= 0 (default 0) */
+  int n_iter;             /* FISTA iterations, >= 1 (default 50) */
+  int n_power;            /* power-method iterations, >= 1 (default 20) */
+} fista_opts;
+void fista_default_opts(fista_opts* opts);
+ashrt_status ashrt_fista(const ashrt_plan* plan, const float* d_dev, const float* trace_mask_dev,
+                         const float* v0_dev, float* m_dev, float* drec_dev, int batch,
+                         const fista_opts* opts, double* lipschitz, void* stream);
+
+/*
  * Autotuner (no counterpart in the paper): times forward+adjoint pairs of
  * `batch` gathers on the plan's sizes for each kernel variant -- the row
  * kernels' form (rows_minb 1, 2 or 3: radix-8 transforms with a register cap

@@ -38,6 +38,10 @@ class IrlsReport(ctypes.Structure):
                 ("flags", c_int), ("misfit", c_double * 64)]
 
 
+class FistaOpts(ctypes.Structure):
+    _fields_ = [("mu", c_double), ("n_iter", c_int), ("n_power", c_int)]
+
+
 class AshrtError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS.get(status, status), msg))
@@ -83,6 +87,11 @@ def load():
                                          P(c_float), c_int, P(AshrtOpts), c_void_p, c_void_p,
                                          c_void_p, c_int, c_void_p]
     lib.ashrt_forward_static.restype = c_int
+    lib.fista_default_opts.argtypes = [P(FistaOpts)]
+    lib.fista_default_opts.restype = None
+    lib.ashrt_fista.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                                P(FistaOpts), P(c_double), c_void_p]
+    lib.ashrt_fista.restype = c_int
     for f in (lib.ashrt_td_forward, lib.ashrt_td_adjoint):
         f.argtypes = [c_int, c_int, c_double, c_double, P(c_float), c_int, P(c_float), c_int,
                       c_void_p, c_void_p, c_int, c_void_p]
@@ -299,6 +308,19 @@ class Plan:
 
     def set_variant(self, rows_minb, xfft_cols):
         _check(load().ashrt_plan_set_variant(self._h, int(rows_minb), int(xfft_cols)))
+
+    def fista(self, d, m, v0, drec=None, mask=None, batch=1, stream=None, mu=0.0, n_iter=50,
+              n_power=20):
+        """ashrt_fista: l2-l1 sparse inversion (FISTA, power-method step).
+        Returns the per-gather Lipschitz constants Lf."""
+        lib = load()
+        o = FistaOpts()
+        lib.fista_default_opts(ctypes.byref(o))
+        o.mu, o.n_iter, o.n_power = float(mu), int(n_iter), int(n_power)
+        lf = (c_double * int(batch))()
+        _check(lib.ashrt_fista(self._h, _ptr(d), _ptr(mask), _ptr(v0), _ptr(m), _ptr(drec),
+                               int(batch), ctypes.byref(o), lf, _stream(stream)))
+        return list(lf)
 
     def deblend(self, d, m, drec=None, batch=1, stream=None, mask=None, apex_mask=None, m0=None,
                 wr0=None, wr_out=None, **kw):
