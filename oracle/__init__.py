@@ -19,4 +19,6 @@ timedomain  time-domain ASHRT / AASHRT hyperbolic summation (ch. 3 Table
 irls        robust l_p-l_q inversion by IRLS with inner CGLS (ch. 4 Eqs
             ch4_cost_fn, equ:10, equ:11, ch4_epcilon_r) and the quality
             measures Q_PD, Q_R (Eqs ch4_Qpd, ch4_Qr).
+fista       l2-l1 inversion by FISTA with a power-method step (ch. 6,
+            "Sparse inversion", Eq. cost_fn with p = 2, q = 1).
 """
