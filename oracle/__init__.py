@@ -15,10 +15,13 @@ stolt       Stolt-based ASHRT / AASHRT forward and its exact transpose
             ch6_adj_operator / ch6_forward_operator).
 timedomain  time-domain ASHRT / AASHRT hyperbolic summation (ch. 3 Table
             ch3_table_Radon_operators, ch. 6 Eqs ch6_AASHRT_forward /
-            ch6_AASHRT_adjoint); used as an independent kinematic check.
+            ch6_AASHRT_adjoint); an independent kinematic check and the
+            reference of the GPU time-domain pair.
 irls        robust l_p-l_q inversion by IRLS with inner CGLS (ch. 4 Eqs
             ch4_cost_fn, equ:10, equ:11, ch4_epcilon_r) and the quality
             measures Q_PD, Q_R (Eqs ch4_Qpd, ch4_Qr).
 fista       l2-l1 inversion by FISTA with a power-method step (ch. 6,
             "Sparse inversion", Eq. cost_fn with p = 2, q = 1).
+unet        the warm-start network (no counterpart in the thesis): forward,
+            hand-derived backward, MSE, Adam, bfloat16 storage rounding.
 """
