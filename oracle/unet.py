@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-The thesis has no learned component; this network is the learned warm start
-of the GB300 build: it maps a pseudo-deblended gather to an initial Radon model
+The thesis has no learned component; this network is the library's learned
+warm start: it maps a pseudo-deblended gather to an initial Radon model
 and initial IRLS residual weights.  Architecture (4 levels, channels ch):
   enc1: conv3x3(cin->c0) relu, conv3x3(c0->c0) relu        -> s1
   avgpool2;  enc2: (c0->c1) relu, (c1->c1) relu            -> s2
