@@ -271,6 +271,30 @@ ashrt_status ashrt_fista(const ashrt_plan* plan, const float* d_dev, const float
                          const fista_opts* opts, double* lipschitz, void* stream);
 
 /*
+ * Acquisition model around the solve (ch. 2, Eqs ch2_blending and
+ * pseudodeblending_equ).  A cube of common-shot gathers D [ns][nr][nt] is
+ * blended into one continuous record per receiver b [nr][nb]; pseudo-
+ * deblending cuts each shot's window back out (the exact transpose); sorting
+ * swaps the two gather axes, [n0][n1][nt] -> [n1][n0][nt] (shot gathers to
+ * the receiver gathers the solve works on, where the interference is
+ * incoherent, and back).
+ *   fire_dev   int32 device array [ns]: firing sample tau_i of shot i (any
+ *              value; samples falling outside [0, nb) are dropped)
+ *   blending        b[r, t'] = sum_i D[i, r, t' - tau_i]  (0 <= t' - tau_i < nt),
+ *                   summed in shot order (no atomics: reproducible)
+ *   pseudo-deblend  D[i, r, t] = b[r, tau_i + t]  (0 <= tau_i + t < nb, else 0)
+ * Asynchronous on `stream`, one launch each, no allocation.  ns <= 8192 for
+ * ashrt_blend; every other count <= 65535.  src and dst of the sort must not
+ * overlap.
+ */
+ashrt_status ashrt_blend(const float* shots_dev, int ns, int nr, int nt, const int* fire_dev,
+                         float* record_dev, int nb, void* stream);
+ashrt_status ashrt_pseudo_deblend(const float* record_dev, int nr, int nb, const int* fire_dev,
+                                  int ns, int nt, float* shots_dev, void* stream);
+ashrt_status ashrt_sort_gathers(const float* src_dev, int n0, int n1, int nt, float* dst_dev,
+                                void* stream);
+
+/*
  * Autotuner (no counterpart in the paper): times forward+adjoint pairs of
  * `batch` gathers on the plan's sizes for each kernel variant -- the row
  * kernels' form (rows_minb 1, 2 or 3: radix-8 transforms with a register cap

@@ -92,6 +92,13 @@ def load():
     lib.ashrt_fista.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                                 P(FistaOpts), P(c_double), c_void_p]
     lib.ashrt_fista.restype = c_int
+    lib.ashrt_blend.argtypes = [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
+                                c_void_p]
+    lib.ashrt_pseudo_deblend.argtypes = [c_void_p, c_int, c_int, c_void_p, c_int, c_int,
+                                         c_void_p, c_void_p]
+    lib.ashrt_sort_gathers.argtypes = [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]
+    for f in (lib.ashrt_blend, lib.ashrt_pseudo_deblend, lib.ashrt_sort_gathers):
+        f.restype = c_int
     for f in (lib.ashrt_td_forward, lib.ashrt_td_adjoint):
         f.argtypes = [c_int, c_int, c_double, c_double, P(c_float), c_int, P(c_float), c_int,
                       c_void_p, c_void_p, c_int, c_void_p]
@@ -225,6 +232,26 @@ def forward_static(nt, nx, dt, dx, velocities, m, d, t0s=None, mask=None, batch=
     _check(lib.ashrt_forward_static(int(nt), int(nx), float(dt), float(dx), vp, va.size, tp,
                                     nt0, ctypes.byref(o), _ptr(m), _ptr(d), _ptr(mask),
                                     int(batch), _stream(stream)))
+
+
+def blend(shots, fire, record, stream=None):
+    """ashrt_blend: shots [ns][nr][nt] -> record [nr][nb]; fire int32 [ns]."""
+    ns, nr, nt = shots.shape
+    _check(load().ashrt_blend(_ptr(shots), ns, nr, nt, _ptr(fire), _ptr(record),
+                              record.shape[-1], _stream(stream)))
+
+
+def pseudo_deblend(record, fire, shots, stream=None):
+    """ashrt_pseudo_deblend: record [nr][nb] -> shots [ns][nr][nt]."""
+    nr, nb = record.shape
+    _check(load().ashrt_pseudo_deblend(_ptr(record), nr, nb, _ptr(fire), shots.shape[0],
+                                       shots.shape[2], _ptr(shots), _stream(stream)))
+
+
+def sort_gathers(src, dst, stream=None):
+    """ashrt_sort_gathers: src [n0][n1][nt] -> dst [n1][n0][nt]."""
+    n0, n1, nt = src.shape
+    _check(load().ashrt_sort_gathers(_ptr(src), n0, n1, nt, _ptr(dst), _stream(stream)))
 
 
 def _td(fn, nt, nx, dt, dx, velocities, src, dst, t0s, batch, stream):
