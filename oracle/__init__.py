@@ -22,6 +22,8 @@ irls        robust l_p-l_q inversion by IRLS with inner CGLS (ch. 4 Eqs
             measures Q_PD, Q_R (Eqs ch4_Qpd, ch4_Qr).
 fista       l2-l1 inversion by FISTA with a power-method step (ch. 6,
             "Sparse inversion", Eq. cost_fn with p = 2, q = 1).
+blending    blending, pseudo-deblending (ch. 2 Eqs ch2_blending,
+            pseudodeblending_equ) and shot <-> receiver gather sorting.
 unet        the warm-start network (no counterpart in the thesis): forward,
             hand-derived backward, MSE, Adam, bfloat16 storage rounding.
 """
