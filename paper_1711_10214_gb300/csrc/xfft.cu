@@ -547,13 +547,14 @@ cudaError_t launch_c2r_pf(const XfftArgs& a, cudaStream_t s, size_t smem) {
 
 // The weight tile goes through shared memory when there is a weight, its
 // rows are 16-byte aligned (nt a multiple of 4) and the CTA's shared memory
-// stays within 160 KB (two CTAs per SM).
+// stays within 100 KB, so that two CTAs still fit on an SM (the register
+// limit of the 512-thread CTAs); larger tiles would halve the occupancy.
 template <int LOGN, int C>
 cudaError_t launch_c2r_v(const XfftArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   const size_t base = (size_t)N * C * sizeof(float2);
   const size_t tile = (size_t)a.nx * 2 * C * sizeof(float);
-  if (a.ew && (a.nt & 3) == 0 && base + tile <= 160 * 1024)
+  if (a.ew && (a.nt & 3) == 0 && base + tile <= 100 * 1024)
     return launch_c2r_pf<LOGN, C, true>(a, s, base + tile);
   return launch_c2r_pf<LOGN, C, false>(a, s, base);
 }
