@@ -12,7 +12,8 @@ Modules
 dft         naive (matrix) discrete Fourier transforms, the F operators.
 stolt       Stolt-based ASHRT / AASHRT forward and its exact transpose
             (ch. 5 Eqs ch5_adj_operator / ch5_forward_operator, ch. 6 Eqs
-            ch6_adj_operator / ch6_forward_operator).
+            ch6_adj_operator / ch6_forward_operator), also for traces at
+            irregular positions (the x transform as a DFT at the traces).
 timedomain  time-domain ASHRT / AASHRT hyperbolic summation (ch. 3 Table
             ch3_table_Radon_operators, ch. 6 Eqs ch6_AASHRT_forward /
             ch6_AASHRT_adjoint); an independent kinematic check and the

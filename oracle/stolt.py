@@ -174,3 +174,56 @@ def adjoint_batch(g, d, mask=None):
     d = np.asarray(d, dtype=np.float64)
     return np.stack([adjoint(g, d[b], None if mask is None else mask[b])
                      for b in range(d.shape[0])])
+
+
+# -- irregular trace positions (ch. 6: "the F operator may be replaced by a
+#    Discrete Fourier Transform operator" for non-uniform spatial sampling) --
+def x_synthesis_matrix(g, x_positions):
+    """E[j, l] = exp(+2 pi i s_l x_j / (Nx dx)) for traces at x_j (metres),
+    s_l the signed wavenumber index of row l; the k_x-Nyquist row l = Nx/2
+    enters as cos(pi x_j / dx), i.e. split evenly between +Nx/2 and -Nx/2
+    (reading: symmetric trigonometric interpolation).  At x_j = j dx this is
+    the regular synthesis matrix."""
+    x = np.asarray(x_positions, dtype=np.float64)[:, None] / (g.Nx * g.dx)
+    s = _dft.signed_index(g.Nx).astype(np.float64)[None, :]
+    E = np.exp(2j * np.pi * s * x)
+    ny = g.Nx // 2
+    E[:, ny] = np.cos(np.pi * np.asarray(x_positions, dtype=np.float64) / g.dx)
+    return E
+
+
+def forward_irregular(g, m, x_positions, mask=None):
+    """d [nr][nt] at irregular trace positions from a model on the regular
+    apex grid: ``forward`` with the x synthesis evaluated at x_positions."""
+    m = np.asarray(m, dtype=np.float64).reshape(g.model_shape)
+    N = g.Nt * g.Nx
+    D = np.zeros((g.Nx, g.Nt), dtype=np.complex128)
+    for j in range(g.nt0):
+        Dj = np.zeros_like(D)
+        for i in range(g.nv):
+            Dj += g.map_forward(_dft.dft2(m[j, i], g.Nx, g.Nt), i)
+        D += g.phase[j][None, :] * Dj
+    D *= g.W[None, :]
+    Et = _dft.dft_matrix(g.nt, g.Nt, +1, g.Nt)
+    d = np.real(x_synthesis_matrix(g, x_positions) @ D @ Et.T) / N
+    if mask is not None:
+        d = d * np.asarray(mask, dtype=np.float64)[:, None]
+    return d
+
+
+def adjoint_irregular(g, d, x_positions, mask=None):
+    """The exact transpose of ``forward_irregular``: the x analysis of the
+    data is the conjugate transpose of the irregular synthesis."""
+    d = np.asarray(d, dtype=np.float64)
+    if mask is not None:
+        d = d * np.asarray(mask, dtype=np.float64)[:, None]
+    N = g.Nt * g.Nx
+    Ft = _dft.dft_matrix(g.Nt, g.nt, -1, g.Nt)
+    Dh = (np.conj(x_synthesis_matrix(g, x_positions)).T @ d @ Ft.T) * (g.W[None, :] / N)
+    m = np.zeros(g.model_shape)
+    for j in range(g.nt0):
+        Dj = np.conj(g.phase[j])[None, :] * Dh
+        for i in range(g.nv):
+            M = g.map_adjoint(Dj, i)
+            m[j, i] = np.real(_dft.idft2_unnormalised(M, g.nx, g.nt))
+    return m
