@@ -124,8 +124,10 @@ ashrt_status ashrt_adjoint(const ashrt_plan* plan, const float* d_dev, float* m_
  * device memory -- a host application that owns the GPU's memory through its
  * own allocator or a fixed budget and passes this library only its input and
  * output buffers, or a latency-critical loop in which a cudaMalloc would
- * synchronise the device.  Computes exactly what ashrt_forward computes for a
- * plan with the same arguments (same kernels, same tables).
+ * synchronise the device.  Computes what ashrt_forward computes for a plan
+ * with the same arguments: the same tables and kernels, with the row kernel
+ * in its radix-8 form (a plan's variant 3; a plan's default for Nt 1024..4096
+ * is the radix-16 forward, which agrees with it to rounding).
  *   nt, nx, dt, dx, velocities/nv, t0_shifts/nt0, opts: as ashrt_plan_create
  *     (apex positions are the trace positions; opts->max_batch and
  *     opts->with_solver are ignored)

@@ -13,7 +13,7 @@
 // model rows and the data spectrum) live in one file-scope __device__ array of
 // kStaticScratchBytes, which every GPU that loads the library keeps for the
 // life of the process.  The caller passes inputs and outputs only.  The kernels
-// are the same ones ashrt_forward launches.
+// are ones ashrt_forward launches too (the row kernel in its radix-8 form).
 #include <cuda_runtime.h>
 
 #include <cmath>
