@@ -66,9 +66,6 @@ def test_time_domain_argument_checks_without_gpu(cdll):
     t0 = (ctypes.c_float * 1)(-0.1,)
     buf = ctypes.c_void_p(16)                      # never dereferenced
     for fn in (cdll.ashrt_td_forward, cdll.ashrt_td_adjoint):
-        fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
-                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         assert fn(1, 8, 0.004, 12.5, v, 2, None, 1, buf, buf, 1, None) == 1
         assert fn(64, 8, 0.004, 12.5, bad_v, 2, None, 1, buf, buf, 1, None) == 1
         assert b"velocity 1" in cdll.ashrt_last_error()
@@ -77,3 +74,20 @@ def test_time_domain_argument_checks_without_gpu(cdll):
         assert fn(64, 8, 0.004, 12.5, v, 2, None, 200, buf, buf, 1, None) == 1
         assert fn(64, 8, 0.004, 12.5, v, 2, None, 1, None, buf, 1, None) == 1
         assert fn(64, 8, -0.004, 12.5, v, 2, None, 1, buf, buf, 1, None) == 1
+
+
+def test_solver_and_acquisition_argument_checks_without_gpu(cdll):
+    """ashrt_fista and the blending / sorting calls reject bad arguments
+    before any CUDA call."""
+    from paper_1711_10214_gb300 import ashrt
+    buf = ctypes.c_void_p(16)                      # never dereferenced
+    assert cdll.ashrt_fista(None, buf, None, buf, buf, None, 1, None, None, None) == 1
+    assert b"NULL plan" in cdll.ashrt_last_error()
+    assert cdll.ashrt_blend(buf, 9000, 4, 64, buf, buf, 100, None) == 1      # too many shots
+    assert cdll.ashrt_blend(buf, 8, 4, 64, None, buf, 100, None) == 1        # no firing times
+    assert cdll.ashrt_pseudo_deblend(buf, 4, 0, buf, 8, 64, buf, None) == 1  # empty record
+    assert cdll.ashrt_sort_gathers(buf, 3, 4, 8, buf, None) == 1             # in place
+    assert b"distinct" in cdll.ashrt_last_error()
+    o = ashrt.FistaOpts()
+    cdll.fista_default_opts(ctypes.byref(o))
+    assert (o.mu, o.n_iter, o.n_power) == (0.0, 50, 20)
