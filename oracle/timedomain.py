@@ -9,13 +9,16 @@ with d read at the fractional time by linear interpolation between samples.
 The forward is the exact transpose of that adjoint (reading of the garbled
 inverse traveltime of Eq. ch6_AASHRT_forward: the path is t = tau0 +
 sqrt(tau^2 + h^2), i.e. tau = sqrt((t - tau0)^2 - h^2)).  Every trace position
-is also an apex position (x_a == x_r == x).  Cost O(nx^2 nt nv nt0)
+is also an apex position (x_a == x_r == x).  Defined for v > 0 and tau0 >= 0
+(the path then starts inside or after the record).  Cost O(nx^2 nt nv nt0)
 (ch. 5, cost of the classical ASHRT).
 """
 import numpy as np
 
 
 def _paths(nt, nx, dt, dx, v, t0):
+    if not (v > 0.0) or not (t0 >= 0.0):
+        raise ValueError("the time-domain pair needs v > 0 and tau0 >= 0")
     tau = np.arange(nt) * dt
     for a in range(nx):
         for r in range(nx):

@@ -1,6 +1,7 @@
 """Pins for the time-domain ASHRT/AASHRT oracle (ch. 3 Table, ch. 6 Eqs
 ch6_AASHRT_forward / ch6_AASHRT_adjoint)."""
 import numpy as np
+import pytest
 from scipy.signal import hilbert
 
 from oracle import stolt, timedomain
@@ -45,3 +46,12 @@ def test_time_domain_and_stolt_agree_kinematically():
             lo, hi = int((tc[j] - 0.06) / DT), int((tc[j] + 0.06) / DT)
             pk = lo + np.argmax(env[j, lo:hi + 1])
             assert abs(pk - np.rint(tc[j] / DT)) <= 2
+
+
+def test_domain_of_the_time_domain_pair():
+    """v > 0 and tau0 >= 0 (the GPU entry points refuse the same inputs)."""
+    m = np.zeros((1, 1, 4, 16))
+    with pytest.raises(ValueError):
+        timedomain.forward(16, 4, DT, DX, [0.0], m)
+    with pytest.raises(ValueError):
+        timedomain.adjoint(16, 4, DT, DX, [1500.0], np.zeros((4, 16)), [-0.01])
