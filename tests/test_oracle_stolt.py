@@ -206,3 +206,99 @@ def test_adjoint_of_data_event_focuses_at_apex():
     env = np.abs(hilbert(m, axis=-1))
     j, i, xa, it = np.unravel_index(np.argmax(env), env.shape)
     assert i == 1 and abs(xa - a) <= 1 and abs(it * DT - tau) <= 2 * DT
+
+
+def _ricker_spectrum(f, f_peak, dt):
+    """Amplitude spectrum of the generator's sampled Ricker wavelet at the
+    frequencies f: the discrete-time Fourier transform of synth.ricker on a
+    symmetric window of +-10/f_peak (the wavelet is even, so the transform
+    is a cosine sum).  Independent of the oracle's closed form."""
+    n = int(np.ceil(10.0 / (f_peak * dt)))
+    t = np.arange(-n, n + 1) * dt
+    r = synth.ricker(t, f_peak)
+    return np.abs(np.cos(2.0 * np.pi * np.outer(np.atleast_1d(f), t)) @ r) * dt
+
+
+@pytest.mark.parametrize("Nt,dt,fp", [(1000, 0.004, 25.0), (2048, 0.004, 25.0),
+                                      (512, 0.004, 20.0), (4096, 0.002, 30.0),
+                                      (256, 0.008, 8.0)])
+def test_spectral_weight_is_the_ricker_amplitude_spectrum(Nt, dt, fp):
+    """The wavelet C of ch. 4 ("a zero phase wavelet with an amplitude
+    spectrum similar to ... the data"): Geometry.W must equal the amplitude
+    spectrum of the Ricker wavelet the generator renders, normalised to 1 at
+    its peak frequency, on every bin of the padded grid; the w-Nyquist bin is
+    0 and the zero-frequency bin is 0.  The spectrum is computed numerically
+    from the sampled wavelet, so a wrong exponent, a missing square or a
+    different normalisation in the oracle fails here."""
+    g = stolt.Geometry(Nt // 4, 8, dt, 12.5, [1500.0], Nt=Nt, Nx=16, wavelet_peak_hz=fp)
+    kk = np.arange(Nt)
+    kk = np.where(kk <= Nt // 2, kk, kk - Nt)
+    f = np.abs(kk) / (Nt * dt)
+    ref = _ricker_spectrum(f, fp, dt) / _ricker_spectrum(fp, fp, dt)
+    ref[Nt // 2] = 0.0
+    np.testing.assert_allclose(g.W, ref, rtol=0, atol=2e-9)
+    assert g.W[0] == 0.0 and g.W[Nt // 2] == 0.0
+    if Nt == 1000:                      # 25 Hz is bin 100 of a 0.25 Hz grid: W = 1 exactly
+        assert g.W[100] == pytest.approx(1.0, abs=1e-15)
+        assert g.W[Nt - 100] == pytest.approx(1.0, abs=1e-15)
+    assert np.all(g.W <= 1.0 + 1e-15)
+    # without the wavelet W is 1 except at the Nyquist bin
+    g0 = stolt.Geometry(Nt // 4, 8, dt, 12.5, [1500.0], Nt=Nt, Nx=16)
+    assert np.all(np.delete(g0.W, Nt // 2) == 1.0) and g0.W[Nt // 2] == 0.0
+
+
+def test_band_limit_edge():
+    """fmax (ch. 5: the map runs over "a limited group of positive
+    frequencies"): |f| > fmax is zeroed in both directions, |f| = fmax and
+    below are kept unchanged.  dt 4 ms, Nt 1000: bins are 0.25 Hz apart, so
+    fmax = 50 Hz is exactly bin 200."""
+    Nt, dt = 1000, 0.004
+    full = stolt.Geometry(250, 8, dt, 12.5, [1500.0], Nt=Nt, Nx=16, wavelet_peak_hz=25.0)
+    lim = stolt.Geometry(250, 8, dt, 12.5, [1500.0], Nt=Nt, Nx=16, wavelet_peak_hz=25.0,
+                         fmax_hz=50.0)
+    keep = np.r_[0:201, Nt - 200:Nt]
+    np.testing.assert_array_equal(lim.W[keep], full.W[keep])
+    assert np.all(lim.W[201:Nt - 200] == 0.0)
+    assert full.W[201] > 0.1 and full.W[Nt - 201] > 0.1
+
+
+@pytest.mark.parametrize("Nt,Nx,v", [(256, 64, 2000.0), (512, 32, 1500.0), (512, 128, 3000.0)])
+def test_adjoint_carries_the_stolt_jacobian(Nt, Nx, v):
+    """ch. 5 Eq. ch5_Stolt_adj: changing the integration variable from w to
+    w_tau brings the factor C = w_tau / w into the adjoint.  The exact
+    transpose of the linear-interpolation map carries it implicitly: each
+    source bin k sends a total weight of 1 to the w_tau bins around
+    u(k) = sqrt(k^2 - a^2), and the sources are dk/du = u / k = w_tau / w per
+    bin.  So the adjoint of a data spike at (t, x) = (0, 0), whose spectrum is
+    flat, has the 2-D spectrum C(w_tau, k_x) = w_tau / sqrt(w_tau^2 + a^2)
+    when averaged over 32 bins (a sanity pin: single bins fluctuate with the
+    interpolation fractions).  Checked on both w sides and both k_x sides,
+    away from the cone edge (C >= 0.4) and from the w-Nyquist bin, without
+    padding so that nothing is cropped; the spectrum is taken with numpy's
+    FFT.  The forward-style gather (C = 1) or an explicit extra C (C^2)
+    misses by more than 10% on every such window."""
+    g = stolt.Geometry(Nt, Nx, DT, DX, [v], Nt=Nt, Nx=Nx)
+    d = np.zeros((Nx, Nt))
+    d[0, 0] = 1.0
+    S = np.fft.fft2(stolt.adjoint(g, d)[0, 0])
+    assert np.max(np.abs(S.imag)) < 1e-12
+    S = S.real
+    H, w = Nt // 2, 32
+    a_all = g.cone_a(v)
+    checked = 0
+    for l in range(1, Nx // 2):
+        a = a_all[l]
+        if a >= H - 1:
+            continue
+        umax = np.sqrt((H - 1) ** 2 - a * a)
+        for j0 in range(1, int(umax) - w - 1, w // 2):
+            jj = np.arange(j0, j0 + w)
+            C = jj / np.sqrt(jj * jj + a * a)
+            if C.min() < 0.4:
+                continue
+            for side in (S[l, jj], S[l, Nt - jj], S[Nx - l, jj]):
+                assert abs(side.mean() - C.mean()) <= 0.05 * C.mean(), (l, j0)
+                checked += 1
+            if C.mean() < 0.85:
+                assert abs(1.0 - C.mean()) > 0.1 * C.mean()
+    assert checked > 300
