@@ -52,6 +52,9 @@ def _args():
     ap.add_argument("--batch", type=int, default=B,
                     help="gathers per call (the deblend workload is 64; smaller batches are "
                          "for profiling captures)")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="deblend mode: row-kernel variant 1..5 instead of the autotuner's "
+                         "choice (profiling captures skip the autotuner's launches this way)")
     ap.add_argument("--rows-variant", type=int, default=0,
                     help="ops mode: row-kernel variant 1..5 (0: the plan's default; see "
                          "ashrt_plan_set_variant)")
@@ -96,6 +99,48 @@ def _peaks():
     hbm = p.get("hbm_gbs")
     return dict(hbm_gbs=hbm if hbm else 6800.0, hbm_src="measured" if hbm else "fallback",
                 sm_max_mhz=p.get("sm_max_mhz", 2070.0))
+
+
+# Source files of each timed kernel class: the committed DRAM-traffic figures
+# (profiles/dram_traffic.md) hold for the sources they were captured from.
+KERNEL_SOURCES = {
+    "stolt_adj_rows": ["stolt_adj.cu", "stolt_r16.cu", "stolt_common.cuh", "common.cuh"],
+    "stolt_fwd_rows": ["stolt_r16.cu", "stolt_fwd.cu", "stolt_common.cuh", "common.cuh"],
+    "xfft_r2c": ["xfft.cu", "tma.cu", "tma.cuh", "common.cuh"],
+    "xfft_c2r": ["xfft.cu", "common.cuh"],
+}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.md")
+
+
+def source_hash(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1711_10214_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(kernel, gathers):
+    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+    of `kernel` over `gathers` gathers, scaled from the committed ncu capture
+    in profiles/dram_traffic.md (rows: | kernel | gathers per launch | bytes
+    per launch | source hash | ...).  None when there is no capture of the
+    kernel's current sources."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rows = [ln.split("|")[1:-1] for ln in f if ln.startswith("| ")]
+    except OSError:
+        return None, None
+    want = source_hash(kernel)
+    for r in rows:
+        r = [x.strip() for x in r]
+        if len(r) >= 4 and r[0] == kernel and r[3] == want:
+            try:
+                return float(r[2]) / float(r[1]) * gathers, want
+            except ValueError:
+                continue
+    return None, want
 
 
 class ClockSampler:
@@ -238,8 +283,17 @@ def run_ours(args):
     # direct launches (not the recorded graph): the roofline needs each kernel
     # bracketed by CUDA events inside the timed region
     kw = dict(p=1.0, q=1.0, n_outer=N_OUTER, n_cg=N_CG)
-    variant = plan.autotune(batch=B, cache_path=os.environ.get(
-        "ASHRT_TUNE_CACHE", "/tmp/ashrt_autotune.jsonl"))
+    if args.variant:
+        plan.set_variant(args.variant, 16)
+        variant = (args.variant, 16)
+    else:
+        variant = plan.autotune(batch=B, cache_path=os.environ.get(
+            "ASHRT_TUNE_CACHE", "/tmp/ashrt_autotune.jsonl"))
+    # FP32 FMA peak of this device, measured with its own clock record
+    pclk = ClockSampler(local)
+    pclk.start()
+    fp32_peak, n_sm = ashrt.fp32_peak(iters=100000, reps=5, stream=stream)
+    peak_clk = pclk.stop()
 
     for _ in range(args.warmup):
         reps = plan.deblend(d, m, drec, batch=B, stream=stream, **kw)
@@ -281,6 +335,12 @@ def run_ours(args):
     te, e2e = whole_job_rate(time.perf_counter() - t0, pairs_per_step * e2e_steps, world, dist,
                              dev)
 
+    # deblending quality of the batch (ch. 4 Eqs ch4_Qpd, ch4_Qr), FP64 on the device
+    clean = torch.from_numpy(c["clean"].astype(np.float32)).to(dev)
+    sums = torch.empty((B, 2), dtype=torch.float64, device=dev)
+    q_pd = ashrt.quality_db(clean, d, sums, stream=stream)
+    q_r = ashrt.quality_db(clean, drec, sums, stream=stream)
+
     if rank != 0:
         return
     alg = algorithmic()
@@ -289,18 +349,13 @@ def run_ours(args):
               key=lambda k: prof[k][0])
     ms, cnt = prof[dom]
     per_launch_s = ms / 1000.0 / max(cnt, 1)
-    alu_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s, FP32 FMA lanes at max clock
+    derived_peak = n_sm * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # FP32 lanes x FMA x max clock
     if dom.startswith("stolt"):
         flops = alg["rows_flops"] * B
     else:
         flops = (NV + 1) * NT * 0.5 * _fft_flops(512) * B
     achieved = flops / per_launch_s / 1e12
-    # DRAM bytes per launch of the dominant kernel, from one ncu capture of the
-    # 8-gather launch of the same kernel (dram__bytes_read.sum +
-    # dram__bytes_write.sum = 672.5 MB for the radix-8 adjoint with its source
-    # table), scaled by the gathers per launch
-    traffic = {"stolt_adj_rows": 672.5e6 / 8}.get(dom)
-    traffic = traffic * B if traffic is not None else None
+    traffic, src_hash = measured_traffic(dom, B)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
@@ -310,9 +365,18 @@ def run_ours(args):
         "hbm_fraction_pair": {"algorithmic_bytes_per_pair": alg["pair_bytes"],
                               "achieved_gbs": value / world * alg["pair_bytes"] / 1e9,
                               "peak_gbs": pk["hbm_gbs"], "peak_src": pk["hbm_src"]},
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                     "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
-                     "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"},
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                     "peak_src": "measured: ashrt_fp32_peak (independent FMA chains on all %d "
+                                 "SMs, best of 5 launches), median SM clock %s MHz during it"
+                                 % (n_sm, peak_clk.get("sm_mhz")),
+                     "derived_peak": derived_peak,
+                     "traffic_src": "profiles/dram_traffic.md, sources %s" % src_hash},
+        "quality": {"q_pd_db_mean": float(np.mean(q_pd)), "q_r_db_mean": float(np.mean(q_r)),
+                    "q_improvement_db_mean": float(np.mean(np.asarray(q_r) - np.asarray(q_pd))),
+                    "q_r_db_min": float(np.min(q_r)),
+                    "what": "Q = 10 log10(|clean|^2 / |clean - x|^2) per gather, x = input "
+                            "(Q_PD) or deblended (Q_R), FP64 device reduction"},
         "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items()},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(d_host.numel() * 4),
                 "d2h_bytes_per_step": int(drec_host.numel() * 4)},

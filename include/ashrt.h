@@ -137,11 +137,15 @@ ashrt_status ashrt_adjoint(const ashrt_plan* plan, const float* d_dev, float* m_
  * exits.  A call whose tables plus workspace exceed it (roughly batch * nv *
  * nt0 * (Nx/2 + 1) * nt * 8 bytes) returns ASHRT_EINVAL with the size it
  * needed.  The call allocates nothing: no cudaMalloc, no cudaFree.
- * The first call on a device looks up that array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture begins.  Every call rewrites the shared array (the tables are
- * uploaded with cudaMemcpyAsync on `stream`), so calls that overlap on the GPU
- * -- on different streams, or from different threads -- race: serialise them.
+ * Each call looks up that array's device address on the current device
+ * (cudaGetSymbolAddress, with the caller's device current), so the entry
+ * point follows cudaSetDevice and survives cudaDeviceReset.  Every call
+ * rewrites the shared array: the tables are uploaded with cudaMemcpyAsync on
+ * `stream` from host memory that lives only for the call, so the call is
+ * refused (ASHRT_EINVAL) while `stream` -- or, for the legacy stream, any
+ * stream of the device -- is being captured into a CUDA graph.  Calls that
+ * overlap on the GPU -- on different streams, or from different threads --
+ * race on the array: serialise them.
  */
 ashrt_status ashrt_forward_static(int nt, int nx, double dt, double dx,
                                   const float* velocities, int nv,
@@ -376,6 +380,36 @@ ashrt_status ashrt_batch_deblend(ashrt_batch* batch, const float* d_dev, float* 
 void ashrt_profile_enable(int on);
 int ashrt_profile_read(double* ms, long long* launches, int n);
 long long ashrt_kernel_launches(void);
+
+/*
+ * FP32 CUDA-core peak of the current device, measured: the roofline
+ * denominator of the ALU-bound row kernels (no counterpart in the paper).
+ * Launches a kernel of independent FMA chains (8 per thread, 2048 threads per
+ * SM on every SM) `reps` + 1 times on `stream` with `iters` loop trips each
+ * (16 x 8 FMAs per trip and thread), times each launch with CUDA events and
+ * returns the best rate after the first in *tflops (2 flops per FMA).
+ * *sm_count (may be NULL) receives the device's SM count.  Synchronises the
+ * stream; allocates no device memory.
+ */
+ashrt_status ashrt_fp32_peak(int iters, int reps, double* tflops, int* sm_count, void* stream);
+
+/*
+ * Deblending quality (ch. 4, Eqs ch4_Qpd and ch4_Qr), per gather:
+ *   Q = 10 log10( ||d_orig||^2 / ||d_orig - d_test||^2 )  [dB]
+ * with d_orig the unblended gather and d_test the pseudo-deblended one (Q_PD)
+ * or the deblended one (Q_R); the improvement of a solve is Q_R - Q_PD.
+ *   d_orig_dev, d_test_dev  [batch][n_per_gather] float32 (read)
+ *   sums_dev   device array [batch][2] of double (written): sum d_orig^2 and
+ *              sum (d_orig - d_test)^2, both accumulated in FP64
+ *   q_db       host array [batch] (written; +inf where the gathers are equal,
+ *              NaN where d_orig is all zero), or NULL: the call is then
+ *              asynchronous on `stream` and leaves only sums_dev.  With q_db
+ *              it synchronises `stream`.
+ * batch <= 65535.  One kernel launch; no allocation.
+ */
+ashrt_status ashrt_quality_db(const float* d_orig_dev, const float* d_test_dev, int batch,
+                              long long n_per_gather, double* sums_dev, double* q_db,
+                              void* stream);
 
 /*
  * Learned warm start (no counterpart in the paper, which starts every solve

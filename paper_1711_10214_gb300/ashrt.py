@@ -157,6 +157,11 @@ def load():
     lib.ashrt_profile_read.restype = c_int
     lib.ashrt_kernel_launches.argtypes = []
     lib.ashrt_kernel_launches.restype = ctypes.c_longlong
+    lib.ashrt_fp32_peak.argtypes = [c_int, c_int, P(c_double), P(c_int), c_void_p]
+    lib.ashrt_fp32_peak.restype = c_int
+    lib.ashrt_quality_db.argtypes = [c_void_p, c_void_p, c_int, ctypes.c_longlong, c_void_p,
+                                     P(c_double), c_void_p]
+    lib.ashrt_quality_db.restype = c_int
     lib.ashrt_status_string.argtypes = [c_int]
     lib.ashrt_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -212,6 +217,27 @@ def profile_read():
 
 def kernel_launches():
     return int(load().ashrt_kernel_launches())
+
+
+def fp32_peak(iters=20000, reps=5, stream=None):
+    """ashrt_fp32_peak: measured FP32 FMA rate of the device, (TFLOP/s, SM count)."""
+    t, n = c_double(), c_int()
+    _check(load().ashrt_fp32_peak(int(iters), int(reps), ctypes.byref(t), ctypes.byref(n),
+                                  _stream(stream)))
+    return t.value, n.value
+
+
+def quality_db(d_orig, d_test, sums, batch=None, stream=None):
+    """ashrt_quality_db: per-gather Q = 10 log10(||d_o||^2 / ||d_o - d_t||^2) in dB
+    (FP64 sums in the device array ``sums`` [batch][2] of float64)."""
+    b = int(batch if batch is not None else d_orig.shape[0])
+    n = d_orig.numel() // d_orig.shape[0]
+    if sums.dtype.itemsize != 8 or not sums.is_cuda or sums.numel() < 2 * b:
+        raise ValueError("sums must be a CUDA float64 tensor of at least 2 * batch elements")
+    q = (c_double * b)()
+    _check(load().ashrt_quality_db(_ptr(d_orig), _ptr(d_test), b, int(n), sums.data_ptr(), q,
+                                   _stream(stream)))
+    return list(q)
 
 
 def forward_static(nt, nx, dt, dx, velocities, m, d, t0s=None, mask=None, batch=1, pad_t=2,

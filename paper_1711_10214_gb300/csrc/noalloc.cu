@@ -17,7 +17,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -26,41 +25,24 @@ namespace ashrt {
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;   // 16 MiB per device
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_static_mu;
-unsigned char* g_static_ptr[kMaxDevices] = {nullptr};
-
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// Device address of the scratch array on the current device; looked up once
-// per device (cudaGetSymbolAddress with that device current).
+// Device address of the scratch array on the current device.  Looked up on
+// every call (cudaGetSymbolAddress with the calling device current; cheap),
+// so nothing is cached across devices or across a cudaDeviceReset.
 ashrt_status static_scratch(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    set_error("ashrt_forward_static: cudaGetDevice failed: %s", cudaGetErrorString(e));
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error("ashrt_forward_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
     return ASHRT_ECUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("ashrt_forward_static: device index %d not supported", dev);
-    return ASHRT_EINVAL;
-  }
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error("ashrt_forward_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return ASHRT_ECUDA;
-    }
-    g_static_ptr[dev] = (unsigned char*)p;
-  }
-  *out = g_static_ptr[dev];
+  *out = (unsigned char*)p;
   return ASHRT_OK;
 }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int log2_ceil(int n) {
   int l = 0;
@@ -90,9 +72,18 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
               "dt > 0, dx > 0, batch >= 1");
     return ASHRT_EINVAL;
   }
-  if (!t0_shifts) nt0 = 1;
-  if (nt0 <= 0) {
+  if (!t0_shifts) {
+    if (nt0 != 1 && nt0 != 0) {
+      set_error("ashrt_forward_static: t0_shifts NULL requires nt0 = 1");
+      return ASHRT_EINVAL;
+    }
+    nt0 = 1;
+  } else if (nt0 <= 0) {
     set_error("ashrt_forward_static: nt0 must be positive");
+    return ASHRT_EINVAL;
+  }
+  if (!(o.fmax_hz >= 0.f) || !(o.wavelet_peak_hz >= 0.f)) {
+    set_error("ashrt_forward_static: fmax_hz and wavelet_peak_hz must be >= 0");
     return ASHRT_EINVAL;
   }
   for (int i = 0; i < nv; ++i)
@@ -127,6 +118,17 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
               "scratch holds %zu bytes (16 MiB); use a plan (ashrt_plan_create) or a smaller "
               "batch / panel count",
               off, kStaticScratchBytes);
+    return ASHRT_EINVAL;
+  }
+  // The host tables below are uploaded from memory that is freed when this
+  // call returns, which a captured graph would read at replay: refuse capture.
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  if (ce != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    set_error("ashrt_forward_static: not usable while a stream capture is active (%s)",
+              ce != cudaSuccess ? cudaGetErrorString(ce) : "the stream is capturing");
     return ASHRT_EINVAL;
   }
   unsigned char* base = nullptr;
@@ -170,7 +172,6 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
     }
   }
 
-  cudaStream_t s = (cudaStream_t)stream;
   auto put = [&](size_t o2, const void* src, size_t bytes) {
     return cudaMemcpyAsync(base + o2, src, bytes, cudaMemcpyHostToDevice, s);
   };

@@ -91,3 +91,31 @@ def test_solver_and_acquisition_argument_checks_without_gpu(cdll):
     o = ashrt.FistaOpts()
     cdll.fista_default_opts(ctypes.byref(o))
     assert (o.mu, o.n_iter, o.n_power) == (0.0, 50, 20)
+
+
+def test_static_forward_and_quality_argument_checks_without_gpu(cdll):
+    """ashrt_forward_static applies the plan's argument rules (t0_shifts NULL
+    only with nt0 = 1, non-negative fmax and wavelet frequency) before any CUDA
+    call; ashrt_quality_db and ashrt_fp32_peak reject bad sizes likewise."""
+    from paper_1711_10214_gb300 import ashrt
+    buf = ctypes.c_void_p(16)                      # never dereferenced
+    v = (ctypes.c_float * 2)(1500.0, 2500.0)
+    o = ashrt.AshrtOpts()
+    cdll.ashrt_default_opts(ctypes.byref(o))
+    fs = cdll.ashrt_forward_static
+    assert fs(64, 16, 0.004, 12.5, v, 2, None, 3, ctypes.byref(o), buf, buf, None, 1, None) == 1
+    assert b"nt0 = 1" in cdll.ashrt_last_error()
+    for field in ("fmax_hz", "wavelet_peak_hz"):
+        bad = ashrt.AshrtOpts()
+        cdll.ashrt_default_opts(ctypes.byref(bad))
+        for val in (-1.0, float("nan")):
+            setattr(bad, field, val)
+            assert fs(64, 16, 0.004, 12.5, v, 2, None, 1, ctypes.byref(bad), buf, buf, None, 1,
+                      None) == 1
+            assert b">= 0" in cdll.ashrt_last_error()
+    sums = ctypes.c_void_p(32)
+    assert cdll.ashrt_quality_db(buf, buf, 0, 10, sums, None, None) == 1
+    assert cdll.ashrt_quality_db(buf, None, 2, 10, sums, None, None) == 1
+    assert cdll.ashrt_quality_db(buf, buf, 2, 10, None, None, None) == 1
+    t = ctypes.c_double()
+    assert cdll.ashrt_fp32_peak(0, 1, ctypes.byref(t), None, None) == 1
