@@ -42,13 +42,21 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="deblend", choices=["deblend", "ops", "unet", "td", "fista",
-                                                         "cube"],
+                                                         "cube", "c3", "c4"],
                     help="ops: forward+adjoint operator pairs only; unet: warm-start U-Net "
                          "inference; td: time-domain (hyperbolic summation) pair against the "
                          "Stolt pair on the same gathers; fista: l2-l1 interpolation by FISTA "
                          "on the gathers with 4 of 5 traces removed; cube: blending, "
                          "pseudo-deblending, sorting and the deblend of a 256-shot x 64-receiver "
-                         "cube (profiling aids)")
+                         "cube; c3: the AASHRT pair with 24 velocities x 16 asymptote "
+                         "shifts on 16 gathers with half the traces removed, and their FISTA "
+                         "interpolation; c4: 2000 gathers of uneven width (nx 96..480, nt "
+                         "1500) deblended through the batch layer, recorded graphs against "
+                         "direct launches (profiling aids and workload runs, not the bench "
+                         "line)")
+    ap.add_argument("--gathers", type=int, default=2000, help="c4: number of gathers")
+    ap.add_argument("--irls", type=int, nargs=2, default=[3, 10],
+                    help="c4: IRLS outer and CG iterations")
     ap.add_argument("--batch", type=int, default=B,
                     help="gathers per call (the deblend workload is 64; smaller batches are "
                          "for profiling captures)")
@@ -607,8 +615,148 @@ def run_cube(args):
     plan.close()
 
 
+def run_c3(args):
+    """c3 workload: AASHRT (24 velocities x 16 asymptote shifts = 384 panels)
+    on 16 gathers of nt 1024 x nx 256 with half of the traces removed (the
+    trace mask S), the velocity sum and phase shift fused in the row kernels;
+    forward + adjoint pairs, then the FISTA interpolation of the gathers (ch. 6
+    "Sparse inversion", 20 power + 30 FISTA iterations) with Q of the
+    interpolated gathers against the complete ones."""
+    import numpy as np
+    import torch
+
+    from paper_1711_10214_gb300 import ashrt, synth
+    dev = torch.device("cuda", 0)
+    nb = min(args.batch, 16)
+    c = synth.config3(nb)
+    plan = ashrt.Plan(NT, NX, DT, DX, c["velocities"], t0s=c["t0s"], wavelet_peak_hz=F_PEAK,
+                      max_batch=nb, with_solver=True)
+    mask = torch.from_numpy(c["mask"]).to(dev)
+    obs = torch.from_numpy(c["observed"].astype(np.float32)).to(dev)
+    clean = torch.from_numpy(c["clean"].astype(np.float32)).to(dev)
+    g = torch.Generator(device=dev).manual_seed(0)
+    m = torch.randn((nb,) + plan.model_shape, device=dev, generator=g)
+    d = torch.empty_like(obs)
+    for _ in range(args.warmup):
+        plan.forward(m, d, mask=mask, batch=nb)
+        plan.adjoint(d, m, mask=mask, batch=nb)
+    torch.cuda.synchronize()
+    ashrt.profile_read()
+    ashrt.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.forward(m, d, mask=mask, batch=nb)
+        plan.adjoint(d, m, mask=mask, batch=nb)
+    e1.record()
+    torch.cuda.synchronize()
+    ashrt.profile_enable(False)
+    prof = ashrt.profile_read()
+    t = e0.elapsed_time(e1) / 1000.0 / args.steps
+    P = plan.P
+    alg = algorithmic(P=P)
+    v0 = torch.randn((nb,) + plan.model_shape, device=dev, generator=g)
+    drec = torch.empty_like(obs)
+    e0.record()
+    plan.fista(obs, m, v0, drec=drec, mask=mask, batch=nb, mu=0.01, n_iter=30, n_power=20)
+    e1.record()
+    torch.cuda.synchronize()
+    t_f = e0.elapsed_time(e1) / 1000.0
+    sums = torch.empty((nb, 2), dtype=torch.float64, device=dev)
+    q_obs = ashrt.quality_db(clean, obs, sums)
+    q_rec = ashrt.quality_db(clean, drec, sums)
+    print(json.dumps({
+        "mode": "c3", "gathers": nb, "panels": P, "nt": NT, "nx": NX,
+        "traces_kept": float(c["mask"].mean()), "pairs_per_s": nb / t,
+        "ms_per_pair_call": 1000.0 * t,
+        "kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+        "pair_tflops": alg["pair_flops"] * nb / t / 1e12,
+        "pair_algorithmic_gbs": alg["pair_bytes"] * nb / t / 1e9,
+        "fista": {"n_power": 20, "n_iter": 30, "s": t_f, "gathers_per_s": nb / t_f,
+                  "q_observed_db_mean": float(np.mean(q_obs)),
+                  "q_interpolated_db_mean": float(np.mean(q_rec))}}), flush=True)
+    plan.close()
+
+
+def run_c4(args):
+    """c4 workload: gathers of uneven width (nx ~ U{96..480}, nt 1500, 5-40
+    events, three dithered interfering sources, 24 velocities, 25 Hz) deblended
+    through the batch layer: classes per padded width Nx, each class streamed
+    through a resident pool of 64 gathers with the autotuned row kernels; the
+    whole pass with recorded graphs (use_graph) and with direct launches."""
+    import numpy as np
+    import torch
+
+    from paper_1711_10214_gb300 import ashrt, synth
+    dev = torch.device("cuda", 0)
+    n, nt = args.gathers, 1500
+    nxs = synth.config4_sizes(n)
+    t0 = time.perf_counter()
+    c = synth.config4(range(n), nxs, nt=nt, processes=os.cpu_count())
+    t_gen = time.perf_counter() - t0
+    b = ashrt.Batch(nt, nxs, DT, DX, c["velocities"], wavelet_peak_hz=F_PEAK, max_resident=64,
+                    with_solver=True)
+    b.autotune(os.environ.get("ASHRT_TUNE_CACHE", "/tmp/ashrt_autotune.jsonl"))
+    d = torch.from_numpy(c["blended"]).to(dev)
+    clean = torch.from_numpy(c["clean"]).to(dev)
+    m = torch.empty(b.model_elems, device=dev)
+    drec = torch.empty_like(d)
+    no, ncg = args.irls
+    kw = dict(p=1.0, q=1.0, n_outer=no, n_cg=ncg)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def run(graph):
+        ev[0].record()
+        reps = b.deblend(d, m, drec, use_graph=graph, **kw)
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1000.0, reps
+
+    run(1)                                        # records the class graphs, loads kernels
+    l0 = ashrt.kernel_launches()
+    t_graph, reps = run(1)
+    l1 = ashrt.kernel_launches()
+    t_direct, _ = run(0)
+    pairs = sum((r["applies_fwd"] + r["applies_adj"]) / 2.0 for r in reps)
+    sums = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    off = 0
+    for g, nx in enumerate(nxs):
+        k = int(nx) * nt
+        ashrt.quality_db(clean[off:off + k], d[off:off + k], sums[g], batch=1, n=k, sync=False)
+        off += k
+    s_pd = sums.cpu().numpy().copy()
+    off = 0
+    for g, nx in enumerate(nxs):
+        k = int(nx) * nt
+        ashrt.quality_db(clean[off:off + k], drec[off:off + k], sums[g], batch=1, n=k, sync=False)
+        off += k
+    s_r = sums.cpu().numpy()
+    q_pd = 10 * np.log10(s_pd[:, 0] / s_pd[:, 1])
+    q_r = 10 * np.log10(s_r[:, 0] / s_r[:, 1])
+    widths = np.array([2 ** int(np.ceil(np.log2(2 * x))) for x in nxs])
+    print(json.dumps({
+        "mode": "c4", "gathers": n, "nt": nt, "nx_range": [int(nxs.min()), int(nxs.max())],
+        "nv": 24, "irls": [no, ncg], "classes": b.n_classes,
+        "gathers_per_class_Nx": {str(w): int((widths == w).sum()) for w in np.unique(widths)},
+        "resident_pool": 64, "device_bytes_held": b.workspace_bytes,
+        "graph": {"s": t_graph, "gathers_per_s": n / t_graph, "pairs_per_s": pairs / t_graph,
+                  "launches": l1 - l0},
+        "direct": {"s": t_direct, "gathers_per_s": n / t_direct, "pairs_per_s": pairs / t_direct},
+        "graph_over_direct_speedup": t_direct / t_graph,
+        "q_pd_db_mean": float(np.mean(q_pd)), "q_r_db_mean": float(np.mean(q_r)),
+        "q_improvement_db_mean": float(np.mean(q_r - q_pd)),
+        "generation_s": t_gen}), flush=True)
+    b.close()
+
+
 def main():
     args = _args()
+    if args.mode == "c3":
+        run_c3(args)
+        return
+    if args.mode == "c4":
+        run_c4(args)
+        return
     if args.mode == "cube":
         run_cube(args)
         return

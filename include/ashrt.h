@@ -350,6 +350,10 @@ ashrt_status ashrt_batch_create_uneven(ashrt_batch** out, const int* nt_per_gath
                                        const float* velocities, int nv, const float* t0_shifts,
                                        int nt0, const ashrt_opts* opts);
 void ashrt_batch_destroy(ashrt_batch* batch);
+/* Runs ashrt_plan_autotune on every class plan at the class's resident batch
+ * (each (nt, Nx) class gets its own row-kernel variant and column tile);
+ * cache_path as there.  Allocates temporary buffers and synchronises. */
+ashrt_status ashrt_batch_autotune(ashrt_batch* batch, const char* cache_path);
 /* Number of Nx classes, packed data / model element counts, device bytes held. */
 ashrt_status ashrt_batch_info(const ashrt_batch* batch, int* n_classes, long long* data_elems,
                               long long* model_elems, size_t* workspace_bytes);

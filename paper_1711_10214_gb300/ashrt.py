@@ -112,6 +112,8 @@ def load():
     lib.ashrt_batch_create_uneven.restype = c_int
     lib.ashrt_batch_destroy.argtypes = [c_void_p]
     lib.ashrt_batch_destroy.restype = None
+    lib.ashrt_batch_autotune.argtypes = [c_void_p, ctypes.c_char_p]
+    lib.ashrt_batch_autotune.restype = c_int
     lib.ashrt_batch_info.argtypes = [c_void_p, P(c_int), P(ctypes.c_longlong),
                                      P(ctypes.c_longlong), P(c_size_t)]
     lib.ashrt_batch_info.restype = c_int
@@ -227,17 +229,19 @@ def fp32_peak(iters=20000, reps=5, stream=None):
     return t.value, n.value
 
 
-def quality_db(d_orig, d_test, sums, batch=None, stream=None):
+def quality_db(d_orig, d_test, sums, batch=None, n=None, sync=True, stream=None):
     """ashrt_quality_db: per-gather Q = 10 log10(||d_o||^2 / ||d_o - d_t||^2) in dB
-    (FP64 sums in the device array ``sums`` [batch][2] of float64)."""
+    (FP64 sums in the device array ``sums`` [batch][2] of float64).  With
+    sync=False the call stays asynchronous, returns None and leaves the sums."""
     b = int(batch if batch is not None else d_orig.shape[0])
-    n = d_orig.numel() // d_orig.shape[0]
-    if sums.dtype.itemsize != 8 or not sums.is_cuda or sums.numel() < 2 * b:
-        raise ValueError("sums must be a CUDA float64 tensor of at least 2 * batch elements")
-    q = (c_double * b)()
-    _check(load().ashrt_quality_db(_ptr(d_orig), _ptr(d_test), b, int(n), sums.data_ptr(), q,
+    n = int(n if n is not None else d_orig.numel() // b)
+    if sums.dtype.itemsize != 8 or not sums.is_cuda or not sums.is_contiguous() or \
+            sums.numel() < 2 * b:
+        raise ValueError("sums must be a contiguous CUDA float64 tensor of >= 2 * batch elements")
+    q = (c_double * b)() if sync else None
+    _check(load().ashrt_quality_db(_ptr(d_orig), _ptr(d_test), b, n, sums.data_ptr(), q,
                                    _stream(stream)))
-    return list(q)
+    return list(q) if sync else None
 
 
 def forward_static(nt, nx, dt, dx, velocities, m, d, t0s=None, mask=None, batch=1, pad_t=2,
@@ -453,6 +457,11 @@ class Batch:
         self.workspace_bytes = ws.value
         self.nt = int(nt) if np.ndim(nt) == 0 else [int(v) for v in nt]
         self.P = self._v.size * nt0
+
+    def autotune(self, cache_path=None):
+        """ashrt_batch_autotune: a kernel variant per (nt, Nx) class."""
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _check(load().ashrt_batch_autotune(self._h, path))
 
     def forward(self, m, d, stream=None):
         _check(load().ashrt_batch_forward(self._h, _ptr(m), _ptr(d), _stream(stream)))

@@ -241,6 +241,18 @@ void ashrt_batch_destroy(ashrt_batch* b) {
   free_batch(b);
 }
 
+ashrt_status ashrt_batch_autotune(ashrt_batch* b, const char* cache_path) {
+  if (!b) {
+    set_error("ashrt_batch_autotune: NULL batch");
+    return ASHRT_EINVAL;
+  }
+  for (auto& c : b->cls) {
+    ashrt_status st = ashrt_plan_autotune(c.plan, c.mb, cache_path, nullptr, nullptr);
+    if (st != ASHRT_OK) return st;
+  }
+  return ASHRT_OK;
+}
+
 ashrt_status ashrt_batch_info(const ashrt_batch* b, int* n_classes, long long* data_elems,
                               long long* model_elems, size_t* workspace_bytes) {
   if (!b) {

@@ -204,6 +204,32 @@ def config4_gather(g, nx, nt=1500):
                    3, 1.5, (1.0, 10.0))
 
 
+def _c4_job(args):
+    g, nx, nt = args
+    c, b = config4_gather(g, nx, nt)
+    return c.astype(np.float32), b.astype(np.float32)
+
+
+def config4(gathers, nxs, nt=1500, processes=0):
+    """c4 gathers for the seeds in `gathers` with trace counts `nxs`: dict with
+    packed clean / blended float32 arrays (gather g is [nx_g][nt] at offset
+    nt * sum_{h<g} nx_h), velocities (24) and f_peak.  processes > 1 renders
+    them in a pool of that many 'spawn' workers."""
+    gathers, nxs = list(gathers), [int(n) for n in nxs]
+    jobs = [(g, nx, nt) for g, nx in zip(gathers, nxs)]
+    if processes and processes > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            res = pool.map(_c4_job, jobs, chunksize=max(1, len(jobs) // (4 * processes)))
+    else:
+        res = [_c4_job(j) for j in jobs]
+    return dict(nt=nt, nxs=nxs, dt=DT, dx=DX,
+                clean=np.concatenate([c.ravel() for c, _ in res]),
+                blended=np.concatenate([b.ravel() for _, b in res]),
+                velocities=velocity_scan(1400.0, 3500.0, 24), t0s=np.zeros(1, np.float32),
+                f_peak=25.0)
+
+
 def random_model(rng, shape, sparsity=None):
     """Random test vector (optionally sparse) for operator parity checks."""
     x = rng.standard_normal(shape)
