@@ -236,6 +236,129 @@ def cpu_baseline_sample():
                        "FP64 numpy naive-DFT oracle; %.1f s" % dt)
 
 
+class ScipyStolt:
+    """The Stolt ASHRT pair as a CPU program on scipy.fft: the fair CPU
+    baseline of the measurement (the same operator as the GPU path and the
+    oracle, with fast transforms instead of the oracle's naive DFTs, all host
+    cores as scipy.fft workers, FP64 or FP32).  Layouts and readings as the
+    library's: real x-transform to the half spectrum (pad nx -> Nx), complex
+    t-transform (pad nt -> Nt), 2-tap linear interpolation in the w index at
+    u = sgn(k) sqrt(k^2 - a^2) inside the cone k^2 > a^2 (taps on the w-Nyquist
+    bin weigh 0), exp(-i w tau0) asymptote phase, Ricker amplitude spectrum
+    W(f) = (f/fp)^2 exp(1 - (f/fp)^2), the adjoint as the exact transpose."""
+
+    def __init__(self, nt, nx, dt, dx, velocities, t0s=(0.0,), wavelet_peak_hz=0.0,
+                 dtype="float64", workers=None):
+        import numpy as np
+        self.np = np
+        self.nt, self.nx, self.dt, self.dx = nt, nx, dt, dx
+        self.Nt = 1 << max(6, (2 * nt - 1).bit_length())
+        self.Nx = 1 << max(4, (2 * nx - 1).bit_length())
+        self.Lh = self.Nx // 2 + 1
+        self.rdt = np.dtype(dtype)
+        self.cdt = np.result_type(self.rdt, np.complex64)
+        self.workers = workers or os.cpu_count()
+        v = np.asarray(velocities, np.float32).astype(np.float64)
+        t0 = np.asarray(t0s, np.float32).astype(np.float64)
+        Nt, Nx, H = self.Nt, self.Nx, self.Nt // 2
+        k = np.arange(Nt)
+        ks = np.where(k <= H, k, k - Nt).astype(np.float64)
+        f = np.abs(ks) / (Nt * dt)
+        W = np.ones(Nt)
+        if wavelet_peak_hz > 0:
+            z = (f / wavelet_peak_hz) ** 2
+            W = z * np.exp(1.0 - z)
+        W[H] = 0.0
+        self.W = W
+        self.phase = [np.exp(-2j * np.pi * ks * tj / (Nt * dt)).astype(self.cdt) for tj in t0]
+        # per velocity: flat source / target indices and weights of the map on [Lh, Nt]
+        self.taps = []
+        rows = np.arange(self.Lh)[:, None]
+        for vi in v:
+            a = ((vi * np.arange(self.Lh, dtype=np.float64)) * float(Nt)) * dt / (float(Nx) * dx)
+            a2 = (a * a)[:, None]
+            cone = (ks[None, :] ** 2 > a2) & (k[None, :] != H)
+            u = np.where(cone, np.sign(ks)[None, :] * np.sqrt(np.maximum(ks[None, :] ** 2 - a2, 0)),
+                         0.0)
+            k0 = np.floor(u)
+            fr = u - k0
+            i0 = np.mod(k0.astype(np.int64), Nt)
+            i1 = np.mod(k0.astype(np.int64) + 1, Nt)
+            w0 = np.where(cone & (i0 != H), 1.0 - fr, 0.0)
+            w1 = np.where(cone & (i1 != H), fr, 0.0)
+            src0 = (rows * Nt + i0).ravel()
+            src1 = (rows * Nt + i1).ravel()
+            self.taps.append((src0, src1, w0.ravel().astype(self.rdt), w1.ravel().astype(self.rdt)))
+
+    def _spec(self, x):
+        import scipy.fft as sf
+        Xh = sf.rfft(x, n=self.Nx, axis=-2, workers=self.workers)
+        return sf.fft(Xh, n=self.Nt, axis=-1, workers=self.workers)
+
+    def forward(self, m):
+        """m [nt0][nv][nx][nt] -> d [nx][nt]."""
+        import scipy.fft as sf
+        np = self.np
+        nt0, nv = m.shape[:2]
+        M = self._spec(m.astype(self.rdt, copy=False)).reshape(nt0, nv, -1)
+        D = np.zeros(self.Lh * self.Nt, self.cdt)
+        for j in range(nt0):
+            Dj = np.zeros_like(D)
+            for i in range(nv):
+                s0, s1, w0, w1 = self.taps[i]
+                Dj += w0 * M[j, i][s0] + w1 * M[j, i][s1]
+            D += Dj * np.tile(self.phase[j], self.Lh)
+        D = D.reshape(self.Lh, self.Nt) * self.W[None, :].astype(self.rdt)
+        y = sf.ifft(D, axis=-1, workers=self.workers)[:, :self.nt]
+        return sf.irfft(y, n=self.Nx, axis=0, workers=self.workers)[:self.nx]
+
+    def adjoint(self, d, nt0, nv):
+        """d [nx][nt] -> m [nt0][nv][nx][nt], the exact transpose of forward."""
+        import scipy.fft as sf
+        np = self.np
+        Dh = (self._spec(d.astype(self.rdt, copy=False)) * self.W[None, :].astype(self.rdt)).ravel()
+        n = self.Lh * self.Nt
+        out = np.empty((nt0, nv, self.nx, self.nt), self.rdt)
+        for j in range(nt0):
+            Dj = Dh * np.tile(np.conj(self.phase[j]), self.Lh)
+            for i in range(nv):
+                s0, s1, w0, w1 = self.taps[i]
+                re = np.bincount(s0, w0 * Dj.real, n) + np.bincount(s1, w1 * Dj.real, n)
+                im = np.bincount(s0, w0 * Dj.imag, n) + np.bincount(s1, w1 * Dj.imag, n)
+                Mi = (re + 1j * im).astype(self.cdt).reshape(self.Lh, self.Nt)
+                # the 1/(Nt Nx) of the pair sits in the inverse transforms here;
+                # the half spectrum is Hermitian in k_x, so the real inverse
+                # transform gives the synthesis over both signs of k_x
+                y = sf.ifft(Mi, axis=-1, workers=self.workers)[:, :self.nt]
+                out[j, i] = sf.irfft(y, n=self.Nx, axis=0, workers=self.workers)[:self.nx]
+        return out
+
+
+def cpu_fft_baseline(nt=NT, nx=NX, nv=NV, reps=2):
+    """The scipy.fft Stolt pair (ScipyStolt) on one gather of the workload,
+    FP64 and FP32, best of `reps` forward + adjoint pairs, all host cores."""
+    import numpy as np
+
+    from paper_1711_10214_gb300 import synth
+    v = synth.velocity_scan(1400.0, 3500.0, nv)
+    rng = np.random.default_rng(0)
+    m = rng.standard_normal((1, nv, nx, nt))
+    d = rng.standard_normal((nx, nt))
+    out = {}
+    for dt_ in ("float64", "float32"):
+        op = ScipyStolt(nt, nx, DT, DX, v, wavelet_peak_hz=F_PEAK, dtype=dt_)
+        best = 1e30
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            op.forward(m)
+            op.adjoint(d, 1, nv)
+            best = min(best, time.perf_counter() - t0)
+        out[dt_] = {"pairs_per_s": 1.0 / best, "s_per_pair": best}
+    return {"kind": "scipy.fft Stolt pair (same operator, fast transforms)",
+            "cores": os.cpu_count(), "workload": "1 gather, nt %d, nx %d, %d velocities" % (nt, nx, nv),
+            "f64": out["float64"], "f32": out["float32"]}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -395,6 +518,7 @@ def run_ours(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
+        line["cpu_fft_baseline"] = cpu_fft_baseline()
     print(json.dumps(line), flush=True)
 
 

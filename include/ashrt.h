@@ -306,9 +306,13 @@ ashrt_status ashrt_sort_gathers(const float* src_dev, int n0, int n1, int nt, fl
  * kernels' form (rows_minb 1, 2 or 3: radix-8 transforms with a register cap
  * for that many resident CTAs per SM, Nt 512..2048; for Nt 1024..4096 also
  * 4: radix-16 forward (three shared-memory passes per transform instead of
- * four) with the radix-8 adjoint, and 5: radix-16 both; the default is 4
- * where it applies, else 3) and the trace-axis FFT column tile (16 or 8
- * columns for Nx <= 512) -- and keeps
+ * four) with the radix-8 adjoint, 5: radix-16 both, 6: radix-16 both with one
+ * gather per CTA instead of an interleaved pair (half the shared memory, so
+ * about twice the resident CTAs; per-bin tables read from L2 instead of
+ * staged), 7: that forward with the radix-8 pair adjoint, 8: the radix-16
+ * pair forward with that adjoint; the default is 4 where it applies, else 3)
+ * and the trace-axis FFT column tile (16 or 8 columns for Nx <= 512) -- and
+ * keeps
  * the fastest in the plan.  With cache_path (a JSON-lines file, one object per
  * device and problem shape) a cached choice is reused without timing and new
  * choices are appended.  Allocates and frees temporary buffers; synchronises.
@@ -317,9 +321,9 @@ ashrt_status ashrt_sort_gathers(const float* src_dev, int n0, int n1, int nt, fl
  */
 ashrt_status ashrt_plan_autotune(ashrt_plan* plan, int batch, const char* cache_path,
                                  int* rows_minb, int* xfft_cols);
-/* Sets the variants directly (rows_minb 1..5, xfft_cols 8 or 16); register
+/* Sets the variants directly (rows_minb 1..8, xfft_cols 8 or 16); register
  * caps and column tiles that do not apply to the plan's sizes fall back to the
- * default kernel; rows_minb 4 or 5 on an Nt other than 1024, 2048 or 4096 is
+ * default kernel; rows_minb 4..8 on an Nt other than 1024, 2048 or 4096 is
  * ASHRT_EINVAL. */
 ashrt_status ashrt_plan_set_variant(ashrt_plan* plan, int rows_minb, int xfft_cols);
 

@@ -31,7 +31,8 @@ std::string tune_key(const ashrt_plan* p, int batch) {
   char name[256] = "unknown";
   if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) snprintf(name, sizeof(name), "%s", prop.name);
   char buf[512];
-  snprintf(buf, sizeof(buf), "%s|nt=%d|nx=%d|Nt=%d|Nx=%d|P=%d|shift=%d|B=%d", name, p->nt, p->nx,
+  snprintf(buf, sizeof(buf), "%s|variants=8|nt=%d|nx=%d|Nt=%d|Nx=%d|P=%d|shift=%d|B=%d", name,
+           p->nt, p->nx,
            p->Nt, p->Nx, p->P, p->shift ? 1 : 0, batch);
   return buf;
 }
@@ -125,8 +126,7 @@ extern "C" ashrt_status ashrt_plan_autotune(ashrt_plan* p, int batch, const char
   std::vector<int> minbs = {3};
   if (p->logNt >= 9 && p->logNt <= 11) minbs = {3, 2, 1};
   if (rows16_supported(p->logNt) && p->tw_t16) {
-    minbs.push_back(4);
-    minbs.push_back(5);
+    for (int v : {4, 5, 6, 7, 8}) minbs.push_back(v);
   }
   std::vector<int> colss = {16};
   if (p->logNx <= 9) colss = {16, 8};
@@ -167,12 +167,13 @@ extern "C" ashrt_status ashrt_plan_autotune(ashrt_plan* p, int batch, const char
 }
 
 extern "C" ashrt_status ashrt_plan_set_variant(ashrt_plan* p, int rows_minb, int xfft_cols) {
-  if (!p || rows_minb < 1 || rows_minb > 5 || (xfft_cols != 8 && xfft_cols != 16)) {
-    set_error("ashrt_plan_set_variant: need a plan, rows_minb in 1..5, xfft_cols 8 or 16");
+  if (!p || rows_minb < 1 || rows_minb > 8 || (xfft_cols != 8 && xfft_cols != 16)) {
+    set_error("ashrt_plan_set_variant: need a plan, rows_minb in 1..8, xfft_cols 8 or 16");
     return ASHRT_EINVAL;
   }
   if (rows_minb >= 4 && !p->tw_t16) {
-    set_error("ashrt_plan_set_variant: the radix-16 row kernels (4, 5) need Nt = 1024, 2048 or 4096");
+    set_error("ashrt_plan_set_variant: the radix-16 row kernels (4..8) need Nt = 1024, 2048 or "
+              "4096");
     return ASHRT_EINVAL;
   }
   p->rows_minb = rows_minb;

@@ -71,7 +71,10 @@ struct RowArgs {
   int batch = 0;
   int minb = 3;                    // variant: 1, 2, 3 radix-8 kernels capped for that many
                                    // resident CTAs per SM; 4 radix-16 forward, radix-8
-                                   // adjoint; 5 radix-16 both (4 and 5 need tw16)
+                                   // adjoint; 5 radix-16 both; 6 single-gather radix-16
+                                   // both; 7 single-gather radix-16 forward, radix-8
+                                   // adjoint; 8 radix-16 pair forward, single-gather
+                                   // radix-16 adjoint (4..8 need tw16)
 };
 
 cudaError_t launch_xfft_r2c(const XfftArgs& a, cudaStream_t s);
@@ -82,6 +85,9 @@ cudaError_t launch_stolt_adj_rows(const RowArgs& a, cudaStream_t s);
 bool rows16_supported(int logNt);
 cudaError_t launch_stolt_fwd_rows16(const RowArgs& a, cudaStream_t s);
 cudaError_t launch_stolt_adj_rows16(const RowArgs& a, cudaStream_t s);
+// Single-gather radix-16 row kernels (Nt = 1024, 2048, 4096; see stolt_r16s.cu).
+cudaError_t launch_stolt_fwd_rows16s(const RowArgs& a, cudaStream_t s);
+cudaError_t launch_stolt_adj_rows16s(const RowArgs& a, cudaStream_t s);
 
 // Stolt tap table: one 32-bit word per (velocity, k_x index l, |k|), |k| in
 // [0, Nt/2].  Mapped bins hold (floor(u) << 20) | round(frac(u) 2^20) with
@@ -155,7 +161,7 @@ struct ashrt_plan {
   int with_solver = 0;
   ashrt_opts opts{};
   bool shift = false;        // any nonzero tau0
-  int rows_minb = 3;         // row-kernel variant 1..5 (autotuned; see ashrt_plan_autotune)
+  int rows_minb = 3;         // row-kernel variant 1..8 (autotuned; see ashrt_plan_autotune)
   int xfft_cols = 16;
   // device tables
   float2* tw_t = nullptr;

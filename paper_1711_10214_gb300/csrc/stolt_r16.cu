@@ -19,194 +19,11 @@
 #include <cuda_runtime.h>
 
 #include "stolt_common.cuh"
+#include "stolt_r16.cuh"
 
 namespace ashrt {
 
 namespace {
-
-constexpr float kCos8 = 0.92387953251128676f;   // cos(pi / 8)
-constexpr float kSin8 = 0.38268343236508977f;   // sin(pi / 8)
-
-// a * (c + DIR i s), both interleaved values
-template <int DIR>
-__device__ __forceinline__ float4 crot(float4 a, float c, float s) {
-  const float sd = DIR < 0 ? -s : s;
-  return make_float4(fmaf(a.x, c, -a.y * sd), fmaf(a.x, sd, a.y * c), fmaf(a.z, c, -a.w * sd),
-                     fmaf(a.z, sd, a.w * c));
-}
-
-// Length-16 DFT as 4 x 4: input n = 4 n1 + n2, output k = k1 + 4 k2,
-//   X[k1 + 4 k2] = sum_n2 W4^(n2 k2) W16^(n2 k1) sum_n1 W4^(n1 k1) x[4 n1 + n2],
-// W_m = exp(DIR 2 pi i / m).
-template <int DIR>
-__device__ __forceinline__ void dft16(float4* v) {
-  float4 y[16];
-#pragma unroll
-  for (int n2 = 0; n2 < 4; ++n2) {
-    float4 a0 = v[n2], a1 = v[n2 + 4], a2 = v[n2 + 8], a3 = v[n2 + 12];
-    dft4<DIR>(a0, a1, a2, a3);
-    y[4 * n2] = a0;
-    y[4 * n2 + 1] = a1;
-    y[4 * n2 + 2] = a2;
-    y[4 * n2 + 3] = a3;
-  }
-  // y[4 n2 + k1] *= W16^(n2 k1)
-  y[5] = crot<DIR>(y[5], kCos8, kSin8);     // W16^1
-  y[6] = mul_eighth<DIR>(y[6]);             // W16^2
-  y[7] = crot<DIR>(y[7], kSin8, kCos8);     // W16^3
-  y[9] = mul_eighth<DIR>(y[9]);             // W16^2
-  y[10] = mul_quarter<DIR>(y[10]);          // W16^4
-  y[11] = mul_3eighth<DIR>(y[11]);          // W16^6
-  y[13] = crot<DIR>(y[13], kSin8, kCos8);   // W16^3
-  y[14] = mul_3eighth<DIR>(y[14]);          // W16^6
-  y[15] = crot<DIR>(y[15], -kCos8, -kSin8); // W16^9 = -W16^1
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) {
-    float4 b0 = y[k1], b1 = y[4 + k1], b2 = y[8 + k1], b3 = y[12 + k1];
-    dft4<DIR>(b0, b1, b2, b3);
-    v[k1] = b0;
-    v[k1 + 4] = b1;
-    v[k1 + 8] = b2;
-    v[k1 + 12] = b3;
-  }
-}
-
-template <int DIR, int R>
-__device__ __forceinline__ void dft16_r(float4* v) {
-  if constexpr (R == 16) dft16<DIR>(v);
-  else dft_r<DIR, R>(v);
-}
-
-// v[r] *= w^r, r = 1..R-1: powers by products of at most four factors,
-// each used for r and r + 8 as soon as it is formed (few live registers).
-template <int R>
-__device__ __forceinline__ void twiddle16_r(float4* v, float2 w) {
-  if constexpr (R == 16) {
-    const float2 w2 = cmul(w, w), w4 = cmul(w2, w2), w8 = cmul(w4, w4);
-    const float2 w3 = cmul(w2, w);
-    v[8] = cmul(v[8], w8);
-    v[1] = cmul(v[1], w);
-    v[9] = cmul(v[9], cmul(w8, w));
-    v[2] = cmul(v[2], w2);
-    v[10] = cmul(v[10], cmul(w8, w2));
-    v[3] = cmul(v[3], w3);
-    v[11] = cmul(v[11], cmul(w8, w3));
-    v[4] = cmul(v[4], w4);
-    v[12] = cmul(v[12], cmul(w8, w4));
-    const float2 w5 = cmul(w4, w);
-    v[5] = cmul(v[5], w5);
-    v[13] = cmul(v[13], cmul(w8, w5));
-    const float2 w6 = cmul(w4, w2);
-    v[6] = cmul(v[6], w6);
-    v[14] = cmul(v[14], cmul(w8, w6));
-    const float2 w7 = cmul(w4, w3);
-    v[7] = cmul(v[7], w7);
-    v[15] = cmul(v[15], cmul(w8, w7));
-  } else {
-    twiddle_r<R>(v, w);
-  }
-}
-
-// Radix schedule of a length 2^LOGN transform: radix 16 while four or more
-// factors of two remain, then one radix 2, 4 or 8 pass.
-template <int LOGN>
-struct Sched16 {
-  static constexpr int N = 1 << LOGN;
-  static constexpr int N16 = LOGN / 4;
-  static constexpr int RL = 1 << (LOGN % 4);
-  static constexpr int NPASS = N16 + (RL > 1 ? 1 : 0);
-  __host__ __device__ static constexpr int radix(int q) { return q < N16 ? 16 : RL; }
-  __host__ __device__ static constexpr int ns(int q) {
-    int s = 1;
-    for (int i = 0; i < q; ++i) s *= radix(i);
-    return s;
-  }
-  __host__ __device__ static constexpr int tw_off(int q) {
-    int o = 0;
-    for (int i = 0; i < q; ++i) o += ns(i);
-    return o;
-  }
-};
-
-__device__ __forceinline__ int swz16(int i) { return swz_g<4>(i); }
-
-// One in-place Stockham pass (see common.cuh for the index rules), T = N/16
-// threads, each with 16 / R butterflies of radix R.
-template <int DIR, int N, int R>
-__device__ __forceinline__ void r16_pass(float4* buf, int Ns, const float2* __restrict__ tw, int off,
-                                         int tid) {
-  constexpr int T = N / 16, NB = 16 / R;
-  float4 v[16];
-#pragma unroll
-  for (int q = 0; q < NB; ++q) {
-    const int jb = tid + T * q;
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz16(jb + r * (N / R))];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NB; ++q) {
-    const int jb = tid + T * q;
-    const int k = jb & (Ns - 1);
-    if (Ns > 1) twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, off, k));
-    dft16_r<DIR, R>(&v[q * R]);
-    const int base = (jb - k) * R + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) buf[swz16(base + r * Ns)] = v[q * R + r];
-  }
-  __syncthreads();
-}
-
-template <int DIR, int LOGN, int Q0, int Q1>
-__device__ __forceinline__ void r16_pass_range(float4* buf, const float2* __restrict__ tw, int tid) {
-  using S = Sched16<LOGN>;
-  if constexpr (Q0 < Q1) {
-    r16_pass<DIR, S::N, S::radix(Q0)>(buf, S::ns(Q0), tw, S::tw_off(Q0), tid);
-    r16_pass_range<DIR, LOGN, Q0 + 1, Q1>(buf, tw, tid);
-  }
-}
-
-// First pass (radix 16, Ns = 1) from registers v[r] = x[tid + r N/16].
-template <int DIR>
-__device__ __forceinline__ void r16_first_pass(float4* buf, float4* v, int tid) {
-  dft16<DIR>(v);
-#pragma unroll
-  for (int r = 0; r < 16; ++r) buf[swz16(tid * 16 + r)] = v[r];
-  __syncthreads();
-}
-
-// Last pass read from shared memory and stored to the global rows outA / outB
-// (outB may be null), keeping outputs with index < n_keep.  Ns = N/R > jb, so
-// output r of butterfly jb is element jb + r Ns.
-template <int DIR, int LOGN>
-__device__ __forceinline__ void r16_last_pass_global(const float4* buf, const float2* __restrict__ tw,
-                                                     int tid, float2* __restrict__ outA,
-                                                     float2* __restrict__ outB, int n_keep) {
-  using S = Sched16<LOGN>;
-  constexpr int Q = S::NPASS - 1, R = S::radix(Q), N = S::N, T = N / 16, NB = 16 / R;
-  constexpr int Ns = S::ns(Q);
-  float4 v[16];
-#pragma unroll
-  for (int q = 0; q < NB; ++q) {
-    const int jb = tid + T * q;
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz16(jb + r * (N / R))];
-  }
-#pragma unroll
-  for (int q = 0; q < NB; ++q) {
-    const int jb = tid + T * q;
-    twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, S::tw_off(Q), jb));
-    dft16_r<DIR, R>(&v[q * R]);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int idx = jb + r * Ns;
-      if (idx < n_keep) {
-        outA[idx] = lo2(v[q * R + r]);
-        if (outB) outB[idx] = hi2(v[q * R + r]);
-      }
-    }
-  }
-}
 
 // Resident CTAs per SM each length is compiled for (register cap 65536 /
 // (threads x CTAs)): Nt 1024 -> 64 threads x 6, 2048 -> 128 x 3, 4096 -> 256 x 1
@@ -270,8 +87,8 @@ stolt_fwd_rows16(RowArgs a) {
       const int k = tid + T * s;
       const Tap t = tap_decode<N>(k, stap[kabs_of<N>(k)]);
       if (t.valid) {
-        float4 vk = cscale(buf[swz16(t.i0)], t.w0);
-        vk = cfma(t.w1, buf[swz16(t.i1)], vk);
+        float4 vk = cscale(buf[swz16<float4>(t.i0)], t.w0);
+        vk = cfma(t.w1, buf[swz16<float4>(t.i1)], vk);
         if (SHIFT) vk = cmul(vk, __ldg(a.phase + (long long)jt * N + k));
         acc[s] = cadd(acc[s], vk);
       }
@@ -325,7 +142,7 @@ stolt_adj_rows16(RowArgs a) {
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
     const int k = tid + T * s;
-    dsp[swz16(k)] = cscale(buf[swz16(k)], __ldg(a.wt + k));
+    dsp[swz16<float4>(k)] = cscale(buf[swz16<float4>(k)], __ldg(a.wt + k));
   }
 
   float2* xA = a.Xw + (long long)b0 * a.x_batch + (long long)l * a.ld;

@@ -29,7 +29,7 @@ def test_every_variant_matches_oracle(lib):
     ref_m = stolt.adjoint_batch(g, d)
     dev = torch.device("cuda:0")
     md, dd = torch.from_numpy(m).to(dev), torch.from_numpy(d).to(dev)
-    for minb in (1, 2, 3, 4, 5):
+    for minb in (1, 2, 3, 4, 5, 6, 7, 8):
         for cols in (8, 16):
             plan.set_variant(minb, cols)
             od, om = torch.empty_like(dd), torch.empty_like(md)
@@ -46,7 +46,7 @@ def test_autotune_choice_and_cache(lib, tmp_path):
     plan = ashrt.Plan(300, 100, DT, DX, [1500.0, 2600.0], max_batch=4)
     cache = str(tmp_path / "tune.jsonl")
     mb, cols = plan.autotune(batch=4, cache_path=cache)
-    assert mb in (1, 2, 3, 4, 5) and cols in (8, 16)
+    assert mb in range(1, 9) and cols in (8, 16)
     lines = [json.loads(x) for x in open(cache)]
     assert len(lines) == 1 and lines[0]["rows_minb"] == mb and lines[0]["xfft_cols"] == cols
     plan2 = ashrt.Plan(300, 100, DT, DX, [1500.0, 2600.0], max_batch=4)
@@ -64,27 +64,61 @@ def test_autotune_choice_and_cache(lib, tmp_path):
     (1024, 17, [0.0, 2500.0], None, 1, False, dict(pad_t=4)),                 # Nt 4096, v = 0, pad 4
 ])
 def test_radix16_rows_match_oracle(lib, nt, nx, v, t0, batch, mask, kw):
-    """The radix-16 row kernels (variant 5: both directions) on every length
-    they serve, with the asymptote shift, the sampling mask and an odd batch
-    (a lone gather in the last pair)."""
+    """The radix-16 row kernels on every length they serve, in both CTA
+    shapes (variant 5: an interleaved gather pair per CTA; variant 6: one
+    gather per CTA, tables read from L2), with the asymptote shift, the
+    sampling mask and an odd batch (a lone gather in the last pair)."""
     import torch
     from paper_1711_10214_gb300 import ashrt
     plan = ashrt.Plan(nt, nx, DT, DX, v, t0s=t0, max_batch=batch, **kw)
-    plan.set_variant(5, 16)
     g = stolt.Geometry(nt, nx, DT, DX, v, t0s=(0.0,) if t0 is None else t0, **kw)
     rng = np.random.default_rng(77)
     m = rng.standard_normal((batch,) + g.model_shape).astype(np.float32)
     d = rng.standard_normal((batch,) + g.data_shape).astype(np.float32)
     mk = (rng.random((batch, nx)) < 0.6).astype(np.float32) if mask else None
+    ref_d, ref_m = stolt.forward_batch(g, m, mk), stolt.adjoint_batch(g, d, mk)
     dev = torch.device("cuda:0")
     md, dd = torch.from_numpy(m).to(dev), torch.from_numpy(d).to(dev)
     mkd = torch.from_numpy(mk).to(dev) if mask else None
-    od, om = torch.empty_like(dd), torch.empty_like(md)
-    plan.forward(md, od, mask=mkd, batch=batch)
-    plan.adjoint(dd, om, mask=mkd, batch=batch)
+    for variant in (5, 6):
+        plan.set_variant(variant, 16)
+        od, om = torch.full_like(dd, float("nan")), torch.full_like(md, float("nan"))
+        plan.forward(md, od, mask=mkd, batch=batch)
+        plan.adjoint(dd, om, mask=mkd, batch=batch)
+        torch.cuda.synchronize()
+        assert _rel(od.cpu().numpy(), ref_d) <= 1e-4, variant
+        assert _rel(om.cpu().numpy(), ref_m) <= 1e-4, variant
+    plan.close()
+
+
+def test_single_gather_rows_dot_test_and_dead_rows(lib):
+    """Variant 6 on the benchmark's row length (Nt 2048) with velocities fast
+    enough that whole (velocity, k_x) rows lie outside the cone (their panel
+    rows are written as zeros without a transform): parity with the oracle and
+    the FP32 dot test <L m, d> = <m, L^T d>."""
+    import torch
+    from paper_1711_10214_gb300 import ashrt
+    nt, nx, v, B = 1000, 40, [1500.0, 6000.0, 9000.0], 3
+    plan = ashrt.Plan(nt, nx, DT, DX, v, max_batch=B, wavelet_peak_hz=25.0)
+    assert plan.Nt == 2048
+    plan.set_variant(6, 16)
+    g = stolt.Geometry(nt, nx, DT, DX, v, wavelet_peak_hz=25.0)
+    a = g.cone_a(9000.0)
+    assert np.sum(a[: g.Nx // 2 + 1] >= g.Nt // 2) > 0       # some rows fully outside
+    rng = np.random.default_rng(78)
+    m = rng.standard_normal((B,) + g.model_shape).astype(np.float32)
+    d = rng.standard_normal((B,) + g.data_shape).astype(np.float32)
+    dev = torch.device("cuda:0")
+    md, dd = torch.from_numpy(m).to(dev), torch.from_numpy(d).to(dev)
+    od, om = torch.full_like(dd, float("nan")), torch.full_like(md, float("nan"))
+    plan.forward(md, od, batch=B)
+    plan.adjoint(dd, om, batch=B)
     torch.cuda.synchronize()
-    assert _rel(od.cpu().numpy(), stolt.forward_batch(g, m, mk)) <= 1e-4
-    assert _rel(om.cpu().numpy(), stolt.adjoint_batch(g, d, mk)) <= 1e-4
+    Lm, LTd = od.cpu().numpy().astype(np.float64), om.cpu().numpy().astype(np.float64)
+    assert _rel(Lm, stolt.forward_batch(g, m)) <= 1e-4
+    assert _rel(LTd, stolt.adjoint_batch(g, d)) <= 1e-4
+    dot = abs(np.vdot(Lm, d) - np.vdot(m, LTd)) / (np.linalg.norm(Lm) * np.linalg.norm(d))
+    assert dot <= 1e-5
     plan.close()
 
 
@@ -93,6 +127,9 @@ def test_radix16_rejected_where_it_does_not_apply(lib):
     plan = ashrt.Plan(100, 20, DT, DX, [2000.0])        # Nt 256
     with pytest.raises(ashrt.AshrtError):
         plan.set_variant(4, 16)
+    for variant in (5, 6, 7, 8):
+        with pytest.raises(ashrt.AshrtError):
+            plan.set_variant(variant, 16)
     with pytest.raises(ashrt.AshrtError):
-        plan.set_variant(5, 16)
+        plan.set_variant(9, 16)
     plan.close()
