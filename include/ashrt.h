@@ -90,6 +90,32 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
                                const float* t0_shifts, int nt0,
                                const ashrt_opts* opts);
 
+/*
+ * Creates a plan whose data traces lie at arbitrary positions (ch. 6: for
+ * irregular spatial sampling the trace-axis Fourier operator F is replaced by
+ * a discrete Fourier transform evaluated at the trace positions).  The model
+ * keeps the regular apex grid x_a = j dx, j < nx (the Stolt map needs it);
+ * the data of every call on this plan is [batch][nr][nt], trace j recorded at
+ * trace_x[j] metres (host array, any finite values, in any order), and trace
+ * masks are [batch][nr].  The forward synthesises each trace from the half
+ * spectrum of the padded apex axis,
+ *   d_j(t) = sum_{l=0}^{Nx/2} c_l Re( exp(+2 pi i l x_j / (Nx dx)) Y_l(t) ),
+ * c_0 = c_{Nx/2} = 1, c_l = 2 otherwise (the Nyquist term enters as
+ * cos(pi x_j / dx)), and the adjoint is its exact transpose; with trace_x[j]
+ * = j dx and nr = nx this is the plan of ashrt_plan_create.  Every other
+ * argument as ashrt_plan_create (apex positions are j dx); max_batch <= 65535.
+ * The data-side transforms are dense contractions costing about
+ * 4 nr nt (Nx/2 + 1) flops per gather and direction.  ashrt_forward,
+ * ashrt_adjoint, robust_irls_deblend and ashrt_fista accept the plan; the
+ * batch layer (ashrt_batch_*) and ashrt_forward_static do not take
+ * irregular traces.
+ */
+ashrt_status ashrt_plan_create_irregular(ashrt_plan** out, int nt, int nx, double dt, double dx,
+                                         const float* velocities, int nv,
+                                         const float* t0_shifts, int nt0,
+                                         const double* trace_x, int nr,
+                                         const ashrt_opts* opts);
+
 /* Frees a plan and its device memory (synchronises the device first). NULL is a no-op. */
 void ashrt_plan_destroy(ashrt_plan* plan);
 

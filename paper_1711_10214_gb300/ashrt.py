@@ -72,6 +72,10 @@ def load():
                                       P(c_float), c_int, P(c_float), c_int, P(c_float), c_int,
                                       P(AshrtOpts)]
     lib.ashrt_plan_create.restype = c_int
+    lib.ashrt_plan_create_irregular.argtypes = [P(c_void_p), c_int, c_int, c_double, c_double,
+                                                P(c_float), c_int, P(c_float), c_int,
+                                                P(c_double), c_int, P(AshrtOpts)]
+    lib.ashrt_plan_create_irregular.restype = c_int
     lib.ashrt_plan_destroy.argtypes = [c_void_p]
     lib.ashrt_plan_destroy.restype = None
     lib.ashrt_plan_info.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int), P(c_size_t)]
@@ -309,7 +313,10 @@ class Plan:
     """A Stolt ASHRT/AASHRT plan (see ashrt_plan_create in include/ashrt.h)."""
 
     def __init__(self, nt, nx, dt, dx, velocities, t0s=None, apex_x=None, pad_t=2, pad_x=2,
-                 fmax_hz=0.0, wavelet_peak_hz=0.0, max_batch=1, with_solver=False):
+                 fmax_hz=0.0, wavelet_peak_hz=0.0, max_batch=1, with_solver=False,
+                 trace_x=None):
+        """trace_x: positions [m] of the data traces (ashrt_plan_create_irregular);
+        None for traces at the apex positions j dx."""
         lib = load()
         o = AshrtOpts()
         lib.ashrt_default_opts(ctypes.byref(o))
@@ -329,8 +336,19 @@ class Plan:
             na = self._ax.size
         h = c_void_p()
         self._h = None
-        _check(lib.ashrt_plan_create(ctypes.byref(h), int(nt), int(nx), float(dt), float(dx),
-                                     vp, self._v.size, ap, na, tp, nt0, ctypes.byref(o)))
+        if trace_x is None:
+            _check(lib.ashrt_plan_create(ctypes.byref(h), int(nt), int(nx), float(dt), float(dx),
+                                         vp, self._v.size, ap, na, tp, nt0, ctypes.byref(o)))
+            self.nr = int(nx)
+        else:
+            if apex_x is not None:
+                raise ValueError("apex_x and trace_x cannot both be given")
+            self._tx = np.ascontiguousarray(np.asarray(trace_x, dtype=np.float64).ravel())
+            _check(lib.ashrt_plan_create_irregular(
+                ctypes.byref(h), int(nt), int(nx), float(dt), float(dx), vp, self._v.size, tp, nt0,
+                self._tx.ctypes.data_as(ctypes.POINTER(c_double)), self._tx.size,
+                ctypes.byref(o)))
+            self.nr = self._tx.size
         self._h = h.value
         self.nt, self.nx, self.nv, self.nt0 = int(nt), int(nx), self._v.size, nt0
         self.max_batch = int(max_batch)
@@ -345,7 +363,7 @@ class Plan:
 
     @property
     def data_shape(self):
-        return (self.nx, self.nt)
+        return (self.nr, self.nt)
 
     def forward(self, m, d, mask=None, batch=1, stream=None):
         _check(load().ashrt_forward(self._h, _ptr(m), _ptr(d), _ptr(mask), int(batch),

@@ -200,7 +200,7 @@ extern "C" ashrt_status ashrt_fista(const ashrt_plan* P, const float* d, const f
     const float beta = (float)((t - 1.0) / t1);
     t = t1;
     FK(op_forward(P, y, q, nullptr, nullptr, tmask, nullptr, B, s));
-    FLAUNCH(k_f_resid, gd, q, d, tmask, P->nx, P->nt);
+    FLAUNCH(k_f_resid, gd, q, d, tmask, P->nr, P->nt);
     FK(op_adjoint(P, q, w, nullptr, nullptr, tmask, nullptr, B, s));
     FLAUNCH(k_f_step, gm, y, w, m, lam, o.mu, beta, nm);
   }

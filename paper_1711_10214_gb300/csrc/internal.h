@@ -112,6 +112,21 @@ void build_tap_rows(const float* velocities, int nv, int Nt, int Nx, int Lh, dou
 inline int atab_row_len(int Nt) { return ((Nt / 2 + 1) + 1) & ~1; }
 bool build_adj_table(const unsigned* taps, const int* kmin, int nv, int Lh, int Nt, uint2* atab);
 
+// Traces at irregular positions (irregular.cu): the data-side trace-axis
+// synthesis d = Re(Es Y) and analysis Yhat = Ea d as dense contractions.
+// Es [nr][Lh] = c_l exp(+2 pi i l x_j / (Nx dx)) (c_l = 2 but 1 at l = 0 and
+// Nx/2; the Nyquist row is cos(pi x_j / dx)); Ea [Lh][nr] = conj of the same
+// without c_l.  Returns false on a non-finite position.
+bool build_irregular_tables(const double* x, int nr, int Nx, double dx, float2* Es, float2* Ea);
+cudaError_t launch_irr_synth(const float2* Es, const float2* Y, float* d, int nr, int nt, int Lh,
+                             int ld, long long y_batch, const float* ew, const float* tmask,
+                             double* dot, int batch, cudaStream_t s);
+cudaError_t launch_irr_analysis(const float2* Ea, const float* d, float2* Yh, int nr, int nt,
+                                int Lh, int ld, long long y_batch, const float* ew,
+                                const float* tmask, int batch, cudaStream_t s);
+cudaError_t launch_irr_cg_r(float* r, const float* q, long long n, const float4* coef, int batch,
+                            cudaStream_t s);
+
 // Twiddle tables in the layout the device passes expect (see common.cuh):
 // radix 2^lr passes while lr or more factors of two remain, then one smaller
 // radix (lr = 3 for the radix-8 kernels, 4 for the radix-16 row kernels).
@@ -155,6 +170,8 @@ struct GraphKey {
 struct ashrt_plan {
   int device = 0;
   int nt = 0, nx = 0, nv = 0, nt0 = 0, P = 0;
+  int nr = 0;                // data traces per gather (= nx unless the traces are irregular)
+  bool irregular = false;    // data traces at given positions (Es / Ea below)
   double dt = 0, dx = 0;
   int Nt = 0, Nx = 0, Lh = 0, ld = 0, logNt = 0, logNx = 0;
   int max_batch = 1;
@@ -173,6 +190,8 @@ struct ashrt_plan {
   unsigned* taps = nullptr;
   uint2* atab = nullptr;
   float2* phase = nullptr;
+  float2* Es = nullptr;      // irregular traces: synthesis table [nr][Lh]
+  float2* Ea = nullptr;      // irregular traces: analysis table [Lh][nr]
   // workspace
   float2* X = nullptr;       // [max_batch][P][Lh][ld]
   float2* Y = nullptr;       // [max_batch][Lh][ld]

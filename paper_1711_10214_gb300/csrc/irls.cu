@@ -481,7 +481,7 @@ int grid_for(long long n_per_gather, int B) {
 // Order statistic machinery: median (mode 0) or eps_r from the MAD (mode 1)
 static cudaError_t select_median(const ashrt_plan* P, const float* x, const float* tm, int B,
                                  int mode, double b_r, double eps_fixed, cudaStream_t s) {
-  const int nx = P->nx, nt = P->nt;
+  const int nx = P->nr, nt = P->nt;   // data traces
   dim3 grid(grid_for((long long)nx * nt, B), B);
   LAUNCH(k_sel_init, B, kThreads, P->sel, P->scal, B);
   for (int shift = 24; shift >= 0; shift -= 8) {
@@ -545,9 +545,9 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
   cudaStream_t s = (cudaStream_t)stream;
   const float* tm = o.trace_mask_dev;
   const float* am = o.apex_mask_dev;
-  const long long nd = (long long)P->nx * P->nt;
-  const long long nm = nd * P->P;
-  const int nx = P->nx, nt = P->nt;
+  const long long nd = (long long)P->nr * P->nt;          // data samples per gather
+  const long long nm = (long long)P->nx * P->nt * P->P;   // model samples per gather
+  const int nx = P->nx, nr = P->nr, nt = P->nt;
   double* scal = P->scal;
   int* flags = P->flags;
   float* r0 = P->qv;   // the IRLS residual shares the CG q buffer (not live at the same time)
@@ -607,7 +607,7 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
           CK(cudaMemsetAsync(scal + S_MIS * B, 0, sizeof(double) * B, s));
           CK(cudaMemsetAsync(scal + S_NLIVE * B, 0, sizeof(double) * B, s));
           CK(cudaMemsetAsync(scal + S_MAXR * B, 0, sizeof(double) * B, s));
-          LAUNCH(k_resid, gd, kThreads, d, P->y, tm, r0, nx, nt, pf, scal, B);
+          LAUNCH(k_resid, gd, kThreads, d, P->y, tm, r0, nr, nt, pf, scal, B);
         }
         if (k == 0 && o.wr0_dev) {
           CK(cudaMemcpyAsync(P->wr, o.wr0_dev, sizeof(float) * nd * B, cudaMemcpyDeviceToDevice, s));
@@ -624,7 +624,7 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
       }
       CK(cudaGetLastError());
       // ---- CGLS on A = W_r S C L W_m^-1, b = W_r S d
-      LAUNCH(k_cg_init_r, gd, kThreads, d, P->y, P->wr, tm, P->r, nx, nt, warm ? 1 : 0);
+      LAUNCH(k_cg_init_r, gd, kThreads, d, P->y, P->wr, tm, P->r, nr, nt, warm ? 1 : 0);
       CK(cudaMemsetAsync(scal + S_GAM0 * B, 0, sizeof(double) * 4 * B, s));
       CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm, o.mu > 0 ? nullptr : scal + S_GAM0 * B, B, s));
       ++applies_a;
@@ -689,7 +689,7 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
       CK(cudaMemsetAsync(scal + S_MIS * B, 0, sizeof(double) * B, s));
       CK(cudaMemsetAsync(scal + S_NLIVE * B, 0, sizeof(double) * B, s));
       CK(cudaMemsetAsync(scal + S_MAXR * B, 0, sizeof(double) * B, s));
-      LAUNCH(k_resid, gd, kThreads, d, P->y, tm, r0, nx, nt, pf, scal, B);
+      LAUNCH(k_resid, gd, kThreads, d, P->y, tm, r0, nr, nt, pf, scal, B);
       LAUNCH(k_outer_done, (B + 127) / 128, 128, scal, flags, outer_cnt, B, k, o.tol);
       CK(cudaGetLastError());
       if (o.tol > 0.0) {

@@ -140,7 +140,7 @@ static ashrt_status cuda_fail(cudaError_t e, const char* what) {
 
 static void free_plan_memory(ashrt_plan* p) {
   void* ptrs[] = {p->tw_t, p->tw_t16, p->tw_x, p->wt, p->kmin, p->acone, p->taps, p->atab,
-                  p->phase, p->X, p->Y, p->u, p->pv, p->sv, p->wminv, p->r, p->qv, p->wr, p->y,
+                  p->phase, p->Es, p->Ea, p->X, p->Y, p->u, p->pv, p->sv, p->wminv, p->r, p->qv, p->wr, p->y,
                   p->scal, p->sel, p->flags, p->cg_coef, p->dev_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -170,7 +170,7 @@ static ashrt_status upload(T** ptr, const std::vector<T>& host, size_t* total) {
 }
 
 size_t model_elems(const ashrt_plan* p) { return (size_t)p->P * p->nx * p->nt; }
-size_t data_elems(const ashrt_plan* p) { return (size_t)p->nx * p->nt; }
+size_t data_elems(const ashrt_plan* p) { return (size_t)p->nr * p->nt; }
 
 // ---------------------------------------------------------------------------
 // Operator application with the fused IRLS weights.
@@ -235,16 +235,21 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
   prof_end(PROF_ROWS_FWD, s);
   if (e != cudaSuccess) return e;
 
-  XfftArgs ay = ax;
-  ay.in_cplx = p->Y;
-  ay.out_real = d;
-  ay.ew = ew_data;
-  ay.tmask = tmask;
-  ay.slabs_per_gather = 1;
-  ay.slabs = batch;
-  ay.dot = dot;
   prof_begin(PROF_XC2R, s);
-  e = launch_xfft_c2r(ay, s);
+  if (p->irregular) {
+    e = launch_irr_synth(p->Es, p->Y, d, p->nr, p->nt, p->Lh, p->ld, ra.y_batch, ew_data, tmask,
+                         dot, batch, s);
+  } else {
+    XfftArgs ay = ax;
+    ay.in_cplx = p->Y;
+    ay.out_real = d;
+    ay.ew = ew_data;
+    ay.tmask = tmask;
+    ay.slabs_per_gather = 1;
+    ay.slabs = batch;
+    ay.dot = dot;
+    e = launch_xfft_c2r(ay, s);
+  }
   prof_end(PROF_XC2R, s);
   return e;
 }
@@ -269,15 +274,30 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
   ay.tw = p->tw_x;
   ay.cols = p->xfft_cols;
   ay.err = p->dev_err;
-  if (cg && cg->mode == 2) {
-    ay.cg_mode = 2;
-    ay.cg_io = const_cast<float*>(d);
-    ay.cg_s = cg->s;
-    ay.cg_coef = cg->coef;
+  cudaError_t e = cudaSuccess;
+  if (p->irregular) {
+    // the CGLS update r -= alpha q runs on its own, then the analysis at the traces
+    if (cg && cg->mode == 2) {
+      e = launch_irr_cg_r(const_cast<float*>(d), cg->s, (long long)p->nr * p->nt, cg->coef,
+                          batch, s);
+      count_launches(1);
+      if (e != cudaSuccess) return e;
+    }
+    prof_begin(PROF_XR2C, s);
+    e = launch_irr_analysis(p->Ea, d, p->Y, p->nr, p->nt, p->Lh, p->ld,
+                            (long long)p->Lh * p->ld, ew_data, tmask, batch, s);
+    prof_end(PROF_XR2C, s);
+  } else {
+    if (cg && cg->mode == 2) {
+      ay.cg_mode = 2;
+      ay.cg_io = const_cast<float*>(d);
+      ay.cg_s = cg->s;
+      ay.cg_coef = cg->coef;
+    }
+    prof_begin(PROF_XR2C, s);
+    e = launch_xfft_r2c(ay, s);
+    prof_end(PROF_XR2C, s);
   }
-  prof_begin(PROF_XR2C, s);
-  cudaError_t e = launch_xfft_r2c(ay, s);
-  prof_end(PROF_XR2C, s);
   if (e != cudaSuccess) return e;
 
   RowArgs ra;
@@ -356,9 +376,14 @@ const char* ashrt_status_string(ashrt_status s) {
   return "ASHRT_UNKNOWN";
 }
 
-ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, double dx,
-                               const float* velocities, int nv, const float* apex_x, int napex,
-                               const float* t0_shifts, int nt0, const ashrt_opts* opts) {
+}  // extern "C"
+
+// Plan creation; xr (host, nr positions in metres) or NULL for traces at the
+// apex positions j dx.
+static ashrt_status plan_create_impl(ashrt_plan** out, int nt, int nx, double dt, double dx,
+                                     const float* velocities, int nv, const float* apex_x,
+                                     int napex, const float* t0_shifts, int nt0,
+                                     const ashrt_opts* opts, const double* xr, int nr) {
   g_err.clear();
   if (!out) {
     set_error("plan_create: out is NULL");
@@ -411,6 +436,17 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
     set_error("plan_create: fmax_hz and wavelet_peak_hz must be >= 0");
     return ASHRT_EINVAL;
   }
+  if (xr) {
+    if (nr < 1 || o.max_batch > 65535) {
+      set_error("plan_create_irregular: need nr >= 1 trace positions and max_batch <= 65535");
+      return ASHRT_EINVAL;
+    }
+    for (int j = 0; j < nr; ++j)
+      if (!std::isfinite(xr[j])) {
+        set_error("plan_create_irregular: trace position %d is not finite", j);
+        return ASHRT_EINVAL;
+      }
+  }
 
   ashrt_plan* p = new ashrt_plan();
   cudaGetDevice(&p->device);
@@ -434,6 +470,8 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
   }
   p->Lh = p->Nx / 2 + 1;
   p->ld = (nt + 3) & ~3;
+  p->irregular = xr != nullptr;
+  p->nr = xr ? nr : nx;
   p->max_batch = o.max_batch;
   p->with_solver = o.with_solver;
   p->opts = o;
@@ -500,6 +538,12 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
   chk(upload(&p->taps, taps, &total));
   chk(upload(&p->atab, atab, &total));
   chk(upload(&p->phase, phase, &total));
+  if (p->irregular) {
+    std::vector<float2> es((size_t)p->nr * Lh), ea((size_t)Lh * p->nr);
+    build_irregular_tables(xr, p->nr, Nx, dx, es.data(), ea.data());
+    chk(upload(&p->Es, es, &total));
+    chk(upload(&p->Ea, ea, &total));
+  }
   const size_t B = (size_t)p->max_batch;
   const size_t xpan = (size_t)Lh * p->ld;
   if (st == ASHRT_OK) chk(dev_alloc(&p->X, B * p->P * xpan, &total));
@@ -536,6 +580,30 @@ ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, doub
   p->ws_bytes = total;
   *out = p;
   return ASHRT_OK;
+}
+
+extern "C" {
+
+ashrt_status ashrt_plan_create(ashrt_plan** out, int nt, int nx, double dt, double dx,
+                               const float* velocities, int nv, const float* apex_x, int napex,
+                               const float* t0_shifts, int nt0, const ashrt_opts* opts) {
+  return plan_create_impl(out, nt, nx, dt, dx, velocities, nv, apex_x, napex, t0_shifts, nt0,
+                          opts, nullptr, 0);
+}
+
+ashrt_status ashrt_plan_create_irregular(ashrt_plan** out, int nt, int nx, double dt, double dx,
+                                         const float* velocities, int nv,
+                                         const float* t0_shifts, int nt0,
+                                         const double* trace_x, int nr,
+                                         const ashrt_opts* opts) {
+  if (!trace_x) {
+    g_err.clear();
+    set_error("plan_create_irregular: trace_x is NULL");
+    if (out) *out = nullptr;
+    return ASHRT_EINVAL;
+  }
+  return plan_create_impl(out, nt, nx, dt, dx, velocities, nv, nullptr, 0, t0_shifts, nt0, opts,
+                          trace_x, nr);
 }
 
 void ashrt_plan_destroy(ashrt_plan* p) {

@@ -119,3 +119,17 @@ def test_static_forward_and_quality_argument_checks_without_gpu(cdll):
     assert cdll.ashrt_quality_db(buf, buf, 2, 10, None, None, None) == 1
     t = ctypes.c_double()
     assert cdll.ashrt_fp32_peak(0, 1, ctypes.byref(t), None, None) == 1
+
+
+def test_irregular_plan_argument_checks_without_gpu(cdll):
+    """ashrt_plan_create_irregular rejects missing or non-finite trace
+    positions and an empty trace set before any CUDA call."""
+    h = ctypes.c_void_p()
+    v = (ctypes.c_float * 1)(1500.0)
+    x = (ctypes.c_double * 3)(0.0, 12.5, float("inf"))
+    f = cdll.ashrt_plan_create_irregular
+    assert f(ctypes.byref(h), 64, 8, 0.004, 12.5, v, 1, None, 1, None, 3, None) == 1
+    assert b"trace_x" in cdll.ashrt_last_error()
+    assert f(ctypes.byref(h), 64, 8, 0.004, 12.5, v, 1, None, 1, x, 0, None) == 1
+    assert f(ctypes.byref(h), 64, 8, 0.004, 12.5, v, 1, None, 1, x, 3, None) == 1
+    assert b"position 2" in cdll.ashrt_last_error() and h.value is None
