@@ -24,6 +24,7 @@ struct XfftArgs {
   const float* tmask = nullptr;      // per-trace weight [gather][nx], or null
   int slabs_per_gather = 1;
   double* dot = nullptr;             // c2r: per-gather sum of squared outputs (added), or null
+  int ew_sq = 0;                     // c2r: store out * ew^2 (dot still sums (out * ew)^2)
   const float2* tw = nullptr;        // base twiddles of length Nx
   int slabs = 0;
   int cols = 16;                     // complex time columns per CTA: 16 or 8 (Nx <= 512)
@@ -45,6 +46,8 @@ struct XfftArgs {
 // A CGLS update to fuse into an operator's first (r2c) transform.
 struct CgFuse {
   int mode = 0;                      // 1: model side (forward), 2: data side (adjoint)
+  int model_ew_sq = 0;               // adjoint: the model-side output is stored times ew_model
+                                     // once more (W_m^-2 L^T ..., the CG's s~ = W_m^-1 s)
   const float* s = nullptr;          // s (mode 1) or q (mode 2)
   float* u = nullptr;                // u (mode 1)
   const float4* coef = nullptr;      // per gather (cs, beta, alpha, -)

@@ -285,13 +285,17 @@ __global__ void k_epsm(double* scal, int B, double b_m, double eps_fixed) {
   scal[S_EPSM * B + g] = e;   // 0 means m == 0: W_m = I
 }
 
-// W_m^-1 = max(|m|, eps_m)^((2-q)/2) (1 when eps_m == 0); u = W_m m (warm) or 0
-__global__ void k_wm(const float* __restrict__ m, float* __restrict__ wminv, float* __restrict__ u,
+// W_m^-1 = max(|m|, eps_m)^((2-q)/2) (1 when eps_m == 0) and the CG start:
+// u = W_m m (warm) or 0; or, when u is null (the fused CG path, which keeps
+// m itself), m is set to the start W_m^-1 u0: 0 on absent apexes and, for a
+// cold CG start, everywhere (gathers stopped on tol keep their model).
+__global__ void k_wm(float* __restrict__ m, float* __restrict__ wminv, float* __restrict__ u,
                      long long n, float q, const double* scal, int B, int warm,
                      const float* __restrict__ amask, int nx, int nt) {
   const int g = blockIdx.y;
   const long long off = (long long)g * n;
   const float e = (float)scal[S_EPSM * B + g];
+  const bool active = scal[S_ACTIVE * B + g] != 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const float mv = m[off + i];
@@ -302,7 +306,8 @@ __global__ void k_wm(const float* __restrict__ m, float* __restrict__ wminv, flo
     }
     if (amask && __ldg(amask + (long long)g * nx + (i / nt) % nx) == 0.f) w = 0.f;
     wminv[off + i] = w;
-    u[off + i] = (warm && w != 0.f) ? mv / w : 0.f;
+    if (u) u[off + i] = (warm && w != 0.f) ? mv / w : 0.f;
+    else if (active && (!warm || w == 0.f)) m[off + i] = 0.f;
   }
 }
 
@@ -545,6 +550,7 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
   cudaStream_t s = (cudaStream_t)stream;
   const float* tm = o.trace_mask_dev;
   const float* am = o.apex_mask_dev;
+  const bool fused = !(o.mu > 0);   // the mu = 0 CG with its updates fused into the transforms
   const long long nd = (long long)P->nr * P->nt;          // data samples per gather
   const long long nm = (long long)P->nx * P->nt * P->P;   // model samples per gather
   const int nx = P->nx, nr = P->nr, nt = P->nt;
@@ -591,9 +597,11 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
     for (int k = 0; k < o.n_outer; ++k) {
       const bool warm = (k > 0 || o.m0_dev) && o.warm_start_cg;
       if (k == 0 && !o.m0_dev) {
-        // cold start: W_m^-1 = 1 (0 on absent apexes), u = 0; W_r = wr0 or 1
-        CK(cudaMemsetAsync(P->u, 0, sizeof(float) * nm * B, s));
-        LAUNCH(k_wm, gm, kThreads, m, P->wminv, P->u, nm, qf, scal, B, 0, am, nx, nt);   // eps_m = 0 -> 1
+        // cold start: W_m^-1 = 1 (0 on absent apexes), u = 0 (m = 0); W_r = wr0 or 1
+        if (fused) CK(cudaMemsetAsync(m, 0, sizeof(float) * nm * B, s));
+        else CK(cudaMemsetAsync(P->u, 0, sizeof(float) * nm * B, s));
+        LAUNCH(k_wm, gm, kThreads, m, P->wminv, fused ? nullptr : P->u, nm, qf, scal, B, 0, am,
+               nx, nt);   // eps_m = 0 -> 1
         LAUNCH(k_set, (B + 127) / 128, 128, scal + S_EPSR * B, 1.0, B);
         if (o.wr0_dev) CK(cudaMemcpyAsync(P->wr, o.wr0_dev, sizeof(float) * nd * B,
                                           cudaMemcpyDeviceToDevice, s));
@@ -620,13 +628,17 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
         CK(cudaMemsetAsync(scal + S_MAXM * B, 0, sizeof(double) * B, s));
         LAUNCH(k_maxabs, gm, kThreads, m, nm, scal, B);
         LAUNCH(k_epsm, (B + 127) / 128, 128, scal, B, o.b_m, o.eps_m_fixed);
-        LAUNCH(k_wm, gm, kThreads, m, P->wminv, P->u, nm, qf, scal, B, warm ? 1 : 0, am, nx, nt);
+        LAUNCH(k_wm, gm, kThreads, m, P->wminv, fused ? nullptr : P->u, nm, qf, scal, B,
+               warm ? 1 : 0, am, nx, nt);
       }
       CK(cudaGetLastError());
       // ---- CGLS on A = W_r S C L W_m^-1, b = W_r S d
       LAUNCH(k_cg_init_r, gd, kThreads, d, P->y, P->wr, tm, P->r, nr, nt, warm ? 1 : 0);
       CK(cudaMemsetAsync(scal + S_GAM0 * B, 0, sizeof(double) * 4 * B, s));
-      CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm, o.mu > 0 ? nullptr : scal + S_GAM0 * B, B, s));
+      CgFuse f0;
+      f0.model_ew_sq = fused ? 1 : 0;     // s~ = W_m^-1 s
+      CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm, o.mu > 0 ? nullptr : scal + S_GAM0 * B, B,
+                    s, &f0));
       ++applies_a;
       if (o.mu > 0) LAUNCH(k_smu, gm, kThreads, P->sv, P->u, nm, muf, scal + S_GAM0 * B, B);
       // The adjoint after the last iteration's update would only serve a
@@ -649,10 +661,14 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
           CK(cudaGetLastError());
         }
       } else {
-        // mu = 0: the vector updates ride on the transforms' loads.  The
-        // forward of iteration it forms p_it = s_it + beta p_{it-1} and applies
-        // the deferred u += alpha_{it-1} p_{it-1}; the adjoint forms
-        // r -= alpha_it q_it.  The last iteration's u update runs on its own.
+        // mu = 0: the vector updates ride on the transforms' loads, and the
+        // vectors are kept premultiplied by W_m^-1: p~ = W_m^-1 p, s~ = W_m^-1 s
+        // and the model m = W_m^-1 u itself, so the forward's input p~ needs no
+        // weight.  The forward of iteration it forms p~_it = s~_it + beta
+        // p~_{it-1} and applies the deferred m += alpha_{it-1} p~_{it-1}; the
+        // adjoint forms r -= alpha_it q_it and returns s~ = W_m^-2 L^T (..) with
+        // gamma = ||W_m^-1 L^T (..)||^2.  The last iteration's m update runs on
+        // its own.
         float4* cf_f = P->cg_coef;
         float4* cf_a = P->cg_coef + B;
         for (int it = 0; it < o.n_cg; ++it) {
@@ -660,13 +676,13 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
           CgFuse ff;
           ff.mode = 1;
           ff.s = P->sv;
-          ff.u = P->u;
+          ff.u = m;
           ff.coef = cf_f;
-          CK(op_forward(P, P->pv, P->qv, P->wminv, P->wr, tm, scal + (S_DEL0 + (it & 1)) * B, B,
+          CK(op_forward(P, P->pv, P->qv, nullptr, P->wr, tm, scal + (S_DEL0 + (it & 1)) * B, B,
                         s, &ff));
           ++applies_f;
           if (it + 1 == o.n_cg) {
-            LAUNCH(k_upd_u, gm, kThreads, P->u, P->pv, nm, scal, B, it);
+            LAUNCH(k_upd_u, gm, kThreads, m, P->pv, nm, scal, B, it);
             break;
           }
           LAUNCH(k_cg_coef_adj, (B + 127) / 128, 128, scal, B, it, cf_a);
@@ -677,13 +693,15 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
           fa.mode = 2;
           fa.s = P->qv;
           fa.coef = cf_a;
+          fa.model_ew_sq = 1;
           CK(op_adjoint(P, P->r, P->sv, P->wminv, P->wr, tm, scal + (S_GAM0 + nxt) * B, B, s, &fa));
           ++applies_a;
           CK(cudaGetLastError());
         }
       }
-      // ---- m = W_m^-1 u, y = C L m (no mask), residual and misfit J_k
-      LAUNCH(k_model, gm, kThreads, m, P->wminv, P->u, nm, scal, B);
+      // ---- m = W_m^-1 u (the fused path keeps m), y = C L m (no mask),
+      //      residual and misfit J_k
+      if (!fused) LAUNCH(k_model, gm, kThreads, m, P->wminv, P->u, nm, scal, B);
       CK(op_forward(P, m, P->y, nullptr, nullptr, nullptr, nullptr, B, s));
       ++applies_f;
       CK(cudaMemsetAsync(scal + S_MIS * B, 0, sizeof(double) * B, s));

@@ -338,6 +338,7 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
   ax.slabs_per_gather = p->P;
   ax.slabs = batch * p->P;
   ax.dot = dot;
+  ax.ew_sq = cg ? cg->model_ew_sq : 0;
   prof_begin(PROF_XC2R, s);
   e = launch_xfft_c2r(ax, s);
   prof_end(PROF_XC2R, s);

@@ -457,16 +457,21 @@ xfft_c2r_kernel(XfftArgs a) {
                         : (ew ? __ldg((const float2*)(ew + o)) : make_float2(1.f, 1.f));
           x.x *= g * e.x;
           x.y *= g * e.y;
-          *(float2*)(out + o) = x;
           ss = fmaf(x.x, x.x, fmaf(x.y, x.y, ss));
+          if (a.ew_sq) {
+            x.x *= e.x;
+            x.y *= e.y;
+          }
+          *(float2*)(out + o) = x;
         } else {
-          const float xa = x.x * g * (PF ? sew[row * 2 * C + 2 * col] : (ew ? __ldg(ew + o) : 1.f));
-          out[o] = xa;
+          const float ea = PF ? sew[row * 2 * C + 2 * col] : (ew ? __ldg(ew + o) : 1.f);
+          const float xa = x.x * g * ea;
+          out[o] = a.ew_sq ? xa * ea : xa;
           ss = fmaf(xa, xa, ss);
           if (ta + 1 < a.nt) {
-            const float xb =
-                x.y * g * (PF ? sew[row * 2 * C + 2 * col + 1] : (ew ? __ldg(ew + o + 1) : 1.f));
-            out[o + 1] = xb;
+            const float eb = PF ? sew[row * 2 * C + 2 * col + 1] : (ew ? __ldg(ew + o + 1) : 1.f);
+            const float xb = x.y * g * eb;
+            out[o + 1] = a.ew_sq ? xb * eb : xb;
             ss = fmaf(xb, xb, ss);
           }
         }
