@@ -40,7 +40,6 @@ struct XfftArgs {
   float* cg_u = nullptr;             // u (mode 1)
   const float4* cg_coef = nullptr;   // [gathers]
   int tma = 1;                       // r2c: use the persistent TMA kernel where it applies
-  int pipe = 1;                      // c2r: use the persistent pipelined kernel where it applies
   int* err = nullptr;                // set to 1 if a bounded device wait ran out
 };
 

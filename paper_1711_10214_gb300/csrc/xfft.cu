@@ -372,73 +372,6 @@ __device__ __forceinline__ float4 herm_load2(const float2* __restrict__ base, in
   return make_float4(ok ? y.x : 0.f, ok ? y.y * sy : 0.f, okb ? y.z : 0.f, okb ? y.w * sy : 0.f);
 }
 
-// Last pass of the c2r transform of one tile, read from the shared [N][C]
-// tile sm and stored to global: output r of butterfly jb is trace jb + r Ns;
-// the real part goes to column ta, the imaginary part to column ta + 1.  The
-// per-element weight comes from the shared tile sew ([nx][2C] floats, PF) or
-// from global memory, times the trace mask; with a.ew_sq the stored value is
-// weighted once more; a.dot accumulates the squared (once-weighted) outputs.
-template <int LOGN, int C, bool PF>
-__device__ __forceinline__ void c2r_last_pass_store(const XfftArgs& a, const float2* sm,
-                                                    const float* sew, long long slab, int ta,
-                                                    int tid) {
-  constexpr int N = 1 << LOGN, T = N * C / 16, JS = T / C;
-  using S = Sched<LOGN>;
-  const int col = tid % C, j0 = tid / C;
-  constexpr int Q = S::NPASS - 1, R = S::radix(Q), NB = 16 / R, Ns = S::ns(Q);
-  float2 w[16];
-#pragma unroll
-  for (int q = 0; q < NB; ++q) {
-    const int jb = j0 + JS * q;
-#pragma unroll
-    for (int r = 0; r < R; ++r) w[q * R + r] = sm[(jb + r * (N / R)) * C + col];
-  }
-  float* out = a.out_real + slab * a.slab_real;
-  const float* ew = a.ew ? a.ew + slab * a.slab_real : nullptr;
-  const float* tm = a.tmask ? a.tmask + (slab / a.slabs_per_gather) * a.nx : nullptr;
-  const bool vec = (a.nt & 1) == 0;
-  float ss = 0.f;
-#pragma unroll
-  for (int q = 0; q < NB; ++q) {
-    const int jb = j0 + JS * q;
-    if (Ns > 1) twiddle_r<R>(&w[q * R], base_twiddle<+1>(a.tw, S::tw_off(Q), jb));
-    dft_r<+1, R>(&w[q * R]);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = jb + r * Ns;
-      if (row < a.nx && ta < a.nt) {
-        const long long o = (long long)row * a.nt + ta;
-        float2 x = w[q * R + r];
-        const float g = tm ? __ldg(tm + row) : 1.f;
-        if (vec && ta + 1 < a.nt) {
-          float2 e = PF ? *(const float2*)(sew + row * 2 * C + 2 * col)
-                        : (ew ? __ldg((const float2*)(ew + o)) : make_float2(1.f, 1.f));
-          x.x *= g * e.x;
-          x.y *= g * e.y;
-          ss = fmaf(x.x, x.x, fmaf(x.y, x.y, ss));
-          if (a.ew_sq) {
-            x.x *= e.x;
-            x.y *= e.y;
-          }
-          *(float2*)(out + o) = x;
-        } else {
-          const float ea = PF ? sew[row * 2 * C + 2 * col] : (ew ? __ldg(ew + o) : 1.f);
-          const float xa = x.x * g * ea;
-          out[o] = a.ew_sq ? xa * ea : xa;
-          ss = fmaf(xa, xa, ss);
-          if (ta + 1 < a.nt) {
-            const float eb = PF ? sew[row * 2 * C + 2 * col + 1] : (ew ? __ldg(ew + o + 1) : 1.f);
-            const float xb = x.y * g * eb;
-            out[o + 1] = a.ew_sq ? xb * eb : xb;
-            ss = fmaf(xb, xb, ss);
-          }
-        }
-      }
-    }
-  }
-  if (a.dot) block_accumulate((double)ss, a.dot + slab / a.slabs_per_gather);
-}
-
 // PF: the tile of the elementwise weight ew that this CTA's outputs use
 // ([nx][2C] floats) is copied into shared memory with cp.async when the CTA
 // starts, so the epilogue reads it from there instead of waiting on global
@@ -492,85 +425,60 @@ xfft_c2r_kernel(XfftArgs a) {
     __syncthreads();
   }
 
-  c2r_last_pass_store<LOGN, C, PF>(a, sm, sew, slab, ta, tid);
-}
-
-// Persistent, software-pipelined form of the weighted c2r (ew present, nt a
-// multiple of 4): each CTA loops over tiles (slab, 2C time columns); the raw
-// half spectrum [Lh][2C] of its next tile and that tile's weights [nx][2C]
-// are copied into shared memory with cp.async while the current tile is
-// transformed and stored, so a tile's loads overlap the previous tile's
-// transform and stores instead of alternating with them.  The weight tiles
-// are double-buffered (the current one is read by the stores while the next
-// one arrives); the spectrum stage is read into registers before the next
-// copy is issued.  Same arithmetic and outputs as xfft_c2r_kernel<.., true>.
-template <int LOGN, int C>
-__global__ void __launch_bounds__((1 << LOGN) * C / 16, 1)
-xfft_c2r_pipe(XfftArgs a, int n_tt, long long n_tiles) {
-  constexpr int N = 1 << LOGN, T = N * C / 16, JS = T / C, H = N / 2;
-  extern __shared__ float2 sm[];                        // [N][C] transform tile
-  float2* stage = sm + N * C;                           // [H + 1][2C] next tile's half spectrum
-  float* wb0 = (float*)(stage + (H + 1) * 2 * C);       // [nx][2C] weights, two buffers
-  float* wb1 = wb0 + a.nx * 2 * C;
-  const int tid = threadIdx.x, col = tid % C, j0 = tid / C;
-  auto issue = [&](long long tl, float* wb) {
-    const long long slab = tl / n_tt;
-    const int t0 = (int)(tl % n_tt) * 2 * C;
-    const float2* in = a.in_cplx + slab * a.slab_cplx;
-    for (int c = tid; c < (H + 1) * C; c += T) {        // C 16-byte chunks per stage row
-      const int row = c / C, q = c % C, t = t0 + 2 * q;
-      if (t < a.ld) cp_async16(stage + row * 2 * C + 2 * q, in + (long long)row * a.ld + t);
-    }
-    const float* ews = a.ew + slab * a.slab_real;
-    constexpr int CPRW = C / 2;                         // 16-byte chunks per weight row
-    for (int c = tid; c < a.nx * CPRW; c += T) {
-      const int row = c / CPRW, q = c % CPRW, t = t0 + 4 * q;
-      if (t < a.nt) cp_async16(wb + row * 2 * C + 4 * q, ews + (long long)row * a.nt + t);
-    }
-    cp_async_commit();
-  };
-  long long tile = blockIdx.x;
-  if (tile < n_tiles) issue(tile, wb0);
-  for (int it = 0; tile < n_tiles; tile += gridDim.x, ++it) {
-    const long long slab = tile / n_tt;
-    const int ta = (int)(tile % n_tt) * 2 * C + 2 * col;
-    const float* wcur = (it & 1) ? wb1 : wb0;
-    cp_async_wait_all();
-    __syncthreads();
-    // first pass inputs: Z = A + i B, A and B the Hermitian-extended spectra
-    // of columns ta, ta + 1 (rows above N/2 mirror row N - row, conjugated;
-    // rows 0 and N/2 keep their real parts)
-    float2 v[2][8];
-    const bool ok = ta < a.nt;                          // then ta + 1 < nt too (nt % 4 == 0)
+  // last pass straight to global: output r of butterfly jb is trace jb + r Ns;
+  // real part -> column ta, imaginary part -> column ta + 1
+  constexpr int Q = S::NPASS - 1, R = S::radix(Q), NB = 16 / R, Ns = S::ns(Q);
+  float2 w[16];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int jb = j0 + JS * q;
+  for (int q = 0; q < NB; ++q) {
+    const int jb = j0 + JS * q;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int row = jb + r * (N / 8);
-        const int rr = row <= H ? row : N - row;
-        float4 y = ok ? *(const float4*)(stage + rr * 2 * C + 2 * col)
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float sy = (row == 0 || row == H) ? 0.f : (row > H ? -1.f : 1.f);
-        y.y *= sy;
-        y.w *= sy;
-        v[q][r] = make_float2(y.x - y.w, y.y + y.z);
+    for (int r = 0; r < R; ++r) w[q * R + r] = sm[(jb + r * (N / R)) * C + col];
+  }
+  float* out = a.out_real + slab * a.slab_real;
+  const float* ew = a.ew ? a.ew + slab * a.slab_real : nullptr;
+  const float* tm = a.tmask ? a.tmask + (slab / a.slabs_per_gather) * a.nx : nullptr;
+  const bool vec = (a.nt & 1) == 0;
+  float ss = 0.f;
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int jb = j0 + JS * q;
+    if (Ns > 1) twiddle_r<R>(&w[q * R], base_twiddle<+1>(a.tw, S::tw_off(Q), jb));
+    dft_r<+1, R>(&w[q * R]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = jb + r * Ns;
+      if (row < a.nx && ta < a.nt) {
+        const long long o = (long long)row * a.nt + ta;
+        float2 x = w[q * R + r];
+        const float g = tm ? __ldg(tm + row) : 1.f;
+        if (vec && ta + 1 < a.nt) {
+          float2 e = PF ? *(const float2*)(sew + row * 2 * C + 2 * col)
+                        : (ew ? __ldg((const float2*)(ew + o)) : make_float2(1.f, 1.f));
+          x.x *= g * e.x;
+          x.y *= g * e.y;
+          ss = fmaf(x.x, x.x, fmaf(x.y, x.y, ss));
+          if (a.ew_sq) {
+            x.x *= e.x;
+            x.y *= e.y;
+          }
+          *(float2*)(out + o) = x;
+        } else {
+          const float ea = PF ? sew[row * 2 * C + 2 * col] : (ew ? __ldg(ew + o) : 1.f);
+          const float xa = x.x * g * ea;
+          out[o] = a.ew_sq ? xa * ea : xa;
+          ss = fmaf(xa, xa, ss);
+          if (ta + 1 < a.nt) {
+            const float eb = PF ? sew[row * 2 * C + 2 * col + 1] : (ew ? __ldg(ew + o + 1) : 1.f);
+            const float xb = x.y * g * eb;
+            out[o + 1] = a.ew_sq ? xb * eb : xb;
+            ss = fmaf(xb, xb, ss);
+          }
+        }
       }
     }
-    __syncthreads();                                    // the stage is free again
-    const long long nxt = tile + gridDim.x;
-    if (nxt < n_tiles) issue(nxt, (it & 1) ? wb0 : wb1);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int jb = j0 + JS * q;
-      dft8<+1>(v[q]);
-#pragma unroll
-      for (int r = 0; r < 8; ++r) sm[(jb * 8 + r) * C + col] = v[q][r];
-    }
-    __syncthreads();
-    col_pass_range<+1, LOGN, C, 1, Sched<LOGN>::NPASS - 1>(sm, a.tw, tid);
-    c2r_last_pass_store<LOGN, C, true>(a, sm, wcur, slab, ta, tid);
   }
+  if (a.dot) block_accumulate((double)ss, a.dot + slab / a.slabs_per_gather);
 }
 
 template <int LOGN, int C>
@@ -642,52 +550,15 @@ cudaError_t launch_c2r_pf(const XfftArgs& a, cudaStream_t s, size_t smem) {
   return cudaGetLastError();
 }
 
-template <int LOGN, int C>
-cudaError_t launch_c2r_pipe(const XfftArgs& a, cudaStream_t s, size_t smem, bool* used) {
-  constexpr int N = 1 << LOGN, T = N * C / 16;
-  *used = false;
-  static size_t attr = 0;
-  if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(xfft_c2r_pipe<LOGN, C>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = smem;
-  }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xfft_c2r_pipe<LOGN, C>, T,
-                                                                smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int n_tt = (a.nt + 2 * C - 1) / (2 * C);
-  const long long n_tiles = (long long)a.slabs * n_tt;
-  const long long grid = std::min<long long>(n_tiles, (long long)sms * per_sm);
-  xfft_c2r_pipe<LOGN, C><<<(unsigned)grid, T, smem, s>>>(a, n_tt, n_tiles);
-  *used = true;
-  return cudaGetLastError();
-}
-
-// A weighted c2r with 16-byte aligned weight rows (nt a multiple of 4) runs
-// as the persistent pipelined kernel when its stage, transform tile and two
-// weight tiles fit in shared memory.  Otherwise the weight tile goes through
-// shared memory when the CTA's shared memory stays within 100 KB, so that
-// two CTAs still fit on an SM (the register limit of the 512-thread CTAs);
-// larger tiles would halve the occupancy.
+// The weight tile goes through shared memory when there is a weight, its
+// rows are 16-byte aligned (nt a multiple of 4) and the CTA's shared memory
+// stays within 100 KB, so that two CTAs still fit on an SM (the register
+// limit of the 512-thread CTAs); larger tiles would halve the occupancy.
 template <int LOGN, int C>
 cudaError_t launch_c2r_v(const XfftArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   const size_t base = (size_t)N * C * sizeof(float2);
   const size_t tile = (size_t)a.nx * 2 * C * sizeof(float);
-  if constexpr (LOGN >= 6 && LOGN <= 10) {
-    const size_t pipe = base + (size_t)(N / 2 + 1) * 2 * C * sizeof(float2) + 2 * tile;
-    if (a.pipe && a.ew && (a.nt & 3) == 0 && pipe <= 200 * 1024) {
-      bool used = false;
-      cudaError_t e = launch_c2r_pipe<LOGN, C>(a, s, pipe, &used);
-      if (e != cudaSuccess || used) return e;
-    }
-  }
   if (a.ew && (a.nt & 3) == 0 && base + tile <= 100 * 1024)
     return launch_c2r_pf<LOGN, C, true>(a, s, base + tile);
   return launch_c2r_pf<LOGN, C, false>(a, s, base);
