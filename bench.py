@@ -42,17 +42,22 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="deblend", choices=["deblend", "ops", "unet", "td", "fista",
-                                                         "cube", "c3", "c4"],
+                                                         "cube", "c1", "c3", "c4", "irregular"],
                     help="ops: forward+adjoint operator pairs only; unet: warm-start U-Net "
                          "inference; td: time-domain (hyperbolic summation) pair against the "
                          "Stolt pair on the same gathers; fista: l2-l1 interpolation by FISTA "
                          "on the gathers with 4 of 5 traces removed; cube: blending, "
                          "pseudo-deblending, sorting and the deblend of a 256-shot x 64-receiver "
-                         "cube; c3: the AASHRT pair with 24 velocities x 16 asymptote "
+                         "cube; c1: the one-gather robust solve (5 x 20) on the GPU, by the "
+                         "FP64 oracle and by the scipy.fft operator on the host cores; c3: the "
+                         "AASHRT pair with 24 velocities x 16 asymptote "
                          "shifts on 16 gathers with half the traces removed, and their FISTA "
                          "interpolation; c4: 2000 gathers of uneven width (nx 96..480, nt "
                          "1500) deblended through the batch layer, recorded graphs against "
-                         "direct launches (profiling aids and workload runs, not the bench "
+                         "direct launches; irregular: the operator pair and the deblend "
+                         "of the workload's gathers recorded at jittered trace positions "
+                         "against the same on the regular grid (profiling aids and workload "
+                         "runs, not the bench "
                          "line)")
     ap.add_argument("--gathers", type=int, default=2000, help="c4: number of gathers")
     ap.add_argument("--irls", type=int, nargs=2, default=[3, 10],
@@ -739,6 +744,117 @@ def run_cube(args):
     plan.close()
 
 
+def run_c1(args):
+    """c1 workload: one 256 x 64 gather, 8 velocities, IRLS 5 x 20 (p = q = 1,
+    20 Hz wavelet): the GPU solve, the FP64 oracle solve and the same solve on
+    the scipy.fft operator (FP64 and FP32), timed; Q of each."""
+    import numpy as np
+    import torch
+
+    from oracle import irls, stolt
+    from paper_1711_10214_gb300 import ashrt, synth
+    dev = torch.device("cuda", 0)
+    c = synth.config1(0)
+    nt, nx, v, fp = c["nt"], c["nx"], c["velocities"], c["f_peak"]
+    kw = dict(p=1.0, q=1.0, n_outer=5, n_cg=20)
+    plan = ashrt.Plan(nt, nx, DT, DX, v, wavelet_peak_hz=fp, with_solver=True)
+    d = torch.from_numpy(c["blended"][None].astype(np.float32)).to(dev)
+    m = torch.empty((1,) + plan.model_shape, device=dev)
+    drec = torch.empty_like(d)
+    for _ in range(args.warmup):
+        reps = plan.deblend(d, m, drec, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        reps = plan.deblend(d, m, drec, **kw)
+    torch.cuda.synchronize()
+    t_gpu = (time.perf_counter() - t0) / args.steps
+    pairs = (reps[0]["applies_fwd"] + reps[0]["applies_adj"]) / 2.0
+    q_gpu = float(irls.q_db(c["clean"], drec[0].cpu().numpy()))
+    g = stolt.Geometry(nt, nx, DT, DX, v, wavelet_peak_hz=fp)
+    d64 = c["blended"].astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    _, rep_o = irls.irls(lambda x: stolt.forward(g, x), lambda r: stolt.adjoint(g, r), d64, **{
+        k: int(v_) if k.startswith("n_") else v_ for k, v_ in kw.items()})
+    t_or = time.perf_counter() - t0
+    out = {"mode": "c1", "nt": nt, "nx": nx, "nv": len(v), "irls": [5, 20],
+           "gpu": {"s_per_solve": t_gpu, "gathers_per_s": 1.0 / t_gpu,
+                   "pairs_per_s": pairs / t_gpu, "q_db": q_gpu},
+           "oracle": {"s_per_solve": t_or, "q_db": float(irls.q_db(c["clean"], rep_o["d_model"])),
+                      "cores": os.cpu_count()},
+           "q_pd_db": float(irls.q_db(c["clean"], c["blended"]))}
+    for dt_ in ("float64", "float32"):
+        op = ScipyStolt(nt, nx, DT, DX, v, wavelet_peak_hz=fp, dtype=dt_)
+        t0 = time.perf_counter()
+        _, rep_s = irls.irls(lambda x: op.forward(x), lambda r: op.adjoint(r, 1, len(v)), d64,
+                             n_outer=5, n_cg=20, p=1, q=1)
+        ts = time.perf_counter() - t0
+        out["cpu_fft_" + dt_] = {"s_per_solve": ts, "q_db": float(irls.q_db(c["clean"],
+                                                                            rep_s["d_model"])),
+                                 "cores": os.cpu_count()}
+    print(json.dumps(out), flush=True)
+    plan.close()
+
+
+def run_irregular(args):
+    """The workload's gathers (64 x nt 1024, 32 velocities, 256 apexes)
+    recorded at 256 jittered trace positions (x_j = (j + U(-0.45, 0.45)) dx):
+    forward + adjoint pairs and the 8 x 30 robust deblend on the irregular
+    plan (data-side x transforms as DFTs at the traces) against the regular
+    plan on the same sizes."""
+    import numpy as np
+    import torch
+
+    from paper_1711_10214_gb300 import ashrt, synth
+    dev = torch.device("cuda", 0)
+    nb = args.batch
+    v = synth.velocity_scan(1400.0, 3500.0, NV)
+    rng = np.random.default_rng(0)
+    x = (np.arange(NX) + rng.uniform(-0.45, 0.45, NX)) * DX
+    c = synth.config2(nb, NT, NX, NV)
+    d = torch.from_numpy(c["blended"].astype(np.float32)).to(dev)
+    out = {"mode": "irregular", "batch": nb, "nt": NT, "nx": NX, "nr": NX, "nv": NV}
+    for name, tx in (("regular", None), ("irregular", x)):
+        plan = ashrt.Plan(NT, NX, DT, DX, v, wavelet_peak_hz=F_PEAK, max_batch=nb,
+                          with_solver=True, trace_x=tx)
+        g = torch.Generator(device=dev).manual_seed(0)
+        m = torch.randn((nb,) + plan.model_shape, device=dev, generator=g)
+        dd = torch.empty_like(d)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(args.warmup):
+            plan.forward(m, dd, batch=nb)
+            plan.adjoint(dd, m, batch=nb)
+        torch.cuda.synchronize()
+        ashrt.profile_read()
+        ashrt.profile_enable(True)
+        e0.record()
+        for _ in range(args.steps):
+            plan.forward(m, dd, batch=nb)
+            plan.adjoint(dd, m, batch=nb)
+        e1.record()
+        torch.cuda.synchronize()
+        ashrt.profile_enable(False)
+        prof = ashrt.profile_read()
+        t = e0.elapsed_time(e1) / 1000.0 / args.steps
+        drec = torch.empty_like(d)
+        plan.deblend(d, m, drec, batch=nb, p=1.0, q=1.0, n_outer=N_OUTER, n_cg=N_CG)
+        torch.cuda.synchronize()
+        e0.record()
+        reps = plan.deblend(d, m, drec, batch=nb, p=1.0, q=1.0, n_outer=N_OUTER, n_cg=N_CG)
+        e1.record()
+        torch.cuda.synchronize()
+        td = e0.elapsed_time(e1) / 1000.0
+        out[name] = {"pairs_per_s": nb / t, "ms_per_pair_call": 1000.0 * t,
+                     "kernel_ms_per_launch": {k: w[0] / max(w[1], 1) for k, w in prof.items()},
+                     "deblend_s": td, "deblend_gathers_per_s": nb / td,
+                     "deblend_pairs_per_s": nb * (reps[0]["applies_fwd"] +
+                                                  reps[0]["applies_adj"]) / 2.0 / td}
+        plan.close()
+    out["irregular_over_regular_time"] = (out["regular"]["pairs_per_s"] /
+                                          out["irregular"]["pairs_per_s"])
+    print(json.dumps(out), flush=True)
+
+
 def run_c3(args):
     """c3 workload: AASHRT (24 velocities x 16 asymptote shifts = 384 panels)
     on 16 gathers of nt 1024 x nx 256 with half of the traces removed (the
@@ -875,6 +991,12 @@ def run_c4(args):
 
 def main():
     args = _args()
+    if args.mode == "c1":
+        run_c1(args)
+        return
+    if args.mode == "irregular":
+        run_irregular(args)
+        return
     if args.mode == "c3":
         run_c3(args)
         return
