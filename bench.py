@@ -117,8 +117,10 @@ def _peaks():
 # Source files of each timed kernel class: the committed DRAM-traffic figures
 # (profiles/dram_traffic.md) hold for the sources they were captured from.
 KERNEL_SOURCES = {
-    "stolt_adj_rows": ["stolt_adj.cu", "stolt_r16.cu", "stolt_common.cuh", "common.cuh"],
-    "stolt_fwd_rows": ["stolt_r16.cu", "stolt_fwd.cu", "stolt_common.cuh", "common.cuh"],
+    "stolt_adj_rows": ["stolt_adj.cu", "stolt_r16.cu", "stolt_r16s.cu", "stolt_r16.cuh",
+                       "stolt_common.cuh", "common.cuh"],
+    "stolt_fwd_rows": ["stolt_r16.cu", "stolt_fwd.cu", "stolt_r16s.cu", "stolt_r16.cuh",
+                       "stolt_common.cuh", "common.cuh"],
     "xfft_r2c": ["xfft.cu", "tma.cu", "tma.cuh", "common.cuh"],
     "xfft_c2r": ["xfft.cu", "common.cuh"],
 }

@@ -117,6 +117,32 @@ __device__ __forceinline__ void dft8(E* v) {
   v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
 }
 
+// dft4 of (v0, v1, 0, 0): the upper half of the inputs is zero.
+template <int DIR, typename E>
+__device__ __forceinline__ void dft4_half(E& v0, E& v1, E& v2, E& v3) {
+  const E a = v0, q = mul_quarter<DIR>(v1);
+  v0 = cadd(a, v1);
+  v2 = csub(a, v1);
+  v1 = cadd(a, q);
+  v3 = csub(a, q);
+}
+
+// dft8 of inputs v[0..3] with v[4..7] = 0 (a zero-padded half).
+template <int DIR, typename E>
+__device__ __forceinline__ void dft8_half(E* v) {
+  E e0 = v[0], e1 = v[2], e2, e3;
+  E o0 = v[1], o1 = v[3], o2, o3;
+  dft4_half<DIR>(e0, e1, e2, e3);
+  dft4_half<DIR>(o0, o1, o2, o3);
+  o1 = mul_eighth<DIR>(o1);
+  o2 = mul_quarter<DIR>(o2);
+  o3 = mul_3eighth<DIR>(o3);
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
 template <int DIR, int R, typename E>
 __device__ __forceinline__ void dft_r(E* v) {
   if constexpr (R == 2) dft2<DIR>(v);
@@ -283,10 +309,12 @@ __device__ __forceinline__ void row_last_pass_global(E* buf, const float2* __res
   }
 }
 
-// First pass (radix 8, Ns = 1, no twiddles) from registers v[r] = x[tid + r N/8].
-template <int DIR, int N, typename E>
+// First pass (radix 8, Ns = 1, no twiddles) from registers v[r] = x[tid + r N/8];
+// HALF: v[4..7] are zero (a row zero-padded to twice its length).
+template <int DIR, int N, typename E, bool HALF = false>
 __device__ __forceinline__ void row_first_pass(E* buf, E* v, int tid) {
-  dft8<DIR>(v);
+  if constexpr (HALF) dft8_half<DIR>(v);
+  else dft8<DIR>(v);
 #pragma unroll
   for (int r = 0; r < 8; ++r) buf[swz_e<E>(tid * 8 + r)] = v[r];
   __syncthreads();

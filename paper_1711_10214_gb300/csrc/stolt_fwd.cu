@@ -38,7 +38,8 @@ namespace {
 // Forward rows.  CTA = (k_x row l, pair of gathers b0, b0+1): the two rows
 // are interleaved element by element, so every shared access is 16 bytes and
 // the twiddles and Stolt taps are computed once for both gathers.
-template <int LOGN, bool SHIFT, int MINB>
+// HALF: nt <= Nt / 2, so inputs tid + r Nt/8 with r >= 4 are zero padding.
+template <int LOGN, bool SHIFT, int MINB, bool HALF>
 __global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
 stolt_fwd_rows(RowArgs a) {
   constexpr int N = 1 << LOGN, T = N / 8;
@@ -75,6 +76,10 @@ stolt_fwd_rows(RowArgs a) {
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = tid + r * T;
+      if (HALF && r >= 4) {
+        v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
       const float2 za = i < a.nt ? stage[i] : make_float2(0.f, 0.f);
       const float2 zb = (hasB && i < a.nt) ? stage[a.ld + i] : make_float2(0.f, 0.f);
       v[r] = pack2(za, zb);
@@ -91,7 +96,7 @@ stolt_fwd_rows(RowArgs a) {
 #pragma unroll
       for (int s = 0; s < 8; ++s) ph[s] = __ldg(a.phase + (long long)jt * N + tid + T * s);
     }
-    row_first_pass<-1, N>(buf, v, tid);
+    row_first_pass<-1, N, float4, HALF>(buf, v, tid);
     row_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw, tid);
 
 #pragma unroll
@@ -121,16 +126,22 @@ stolt_fwd_rows(RowArgs a) {
 }
 
 
-template <int LOGN, bool SHIFT, int MINB>
-cudaError_t launch_fwd_v(const RowArgs& a, cudaStream_t s) {
+template <int LOGN, bool SHIFT, int MINB, bool HALF>
+cudaError_t launch_fwd_vh(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
   const size_t smem = (size_t)N * sizeof(float4) + (size_t)2 * a.ld * sizeof(float2) +
                       (size_t)2 * a.taps_ld * sizeof(unsigned);
-  cudaError_t e = set_smem(stolt_fwd_rows<LOGN, SHIFT, MINB>, smem_cap<LOGN>(true), attr);
+  cudaError_t e = set_smem(stolt_fwd_rows<LOGN, SHIFT, MINB, HALF>, smem_cap<LOGN>(true), attr);
   if (e != cudaSuccess) return e;
-  stolt_fwd_rows<LOGN, SHIFT, MINB><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
+  stolt_fwd_rows<LOGN, SHIFT, MINB, HALF><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int LOGN, bool SHIFT, int MINB>
+cudaError_t launch_fwd_v(const RowArgs& a, cudaStream_t s) {
+  return 2 * a.nt <= a.Nt ? launch_fwd_vh<LOGN, SHIFT, MINB, true>(a, s)
+                          : launch_fwd_vh<LOGN, SHIFT, MINB, false>(a, s);
 }
 
 // Register-cap variant: resident CTAs per SM the kernel is compiled for

@@ -33,8 +33,10 @@ constexpr int r16_minb() {
   return LOGN == 10 ? 6 : (LOGN == 11 ? 3 : 1);
 }
 
-// Forward rows: as stolt_fwd_rows, with 16 bins per thread.
-template <int LOGN, bool SHIFT>
+// Forward rows: as stolt_fwd_rows, with 16 bins per thread.  HALF: nt <=
+// Nt / 2, so the staged panel fills only the first half of each transform
+// (inputs tid + r Nt/16 with r >= 8 are zero padding).
+template <int LOGN, bool SHIFT, bool HALF>
 __global__ void __launch_bounds__((1 << LOGN) / 16, r16_minb<LOGN>())
 stolt_fwd_rows16(RowArgs a) {
   constexpr int N = 1 << LOGN, T = N / 16;
@@ -67,6 +69,10 @@ stolt_fwd_rows16(RowArgs a) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int i = tid + r * T;
+      if (HALF && r >= 8) {
+        v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
       const float2 za = i < a.nt ? stage[i] : make_float2(0.f, 0.f);
       const float2 zb = (hasB && i < a.nt) ? stage[a.ld + i] : make_float2(0.f, 0.f);
       v[r] = pack2(za, zb);
@@ -79,7 +85,7 @@ stolt_fwd_rows16(RowArgs a) {
       stage_taps((p & 1) ? stap0 : stap1, trow + ivn * tstep, a.taps_ld, tid, T);
       cp_async_commit();
     }
-    r16_first_pass<-1>(buf, v, tid);
+    r16_first_pass<-1, float4, HALF>(buf, v, tid);
     r16_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw16, tid);
 
 #pragma unroll
@@ -176,16 +182,22 @@ stolt_adj_rows16(RowArgs a) {
   }
 }
 
-template <int LOGN, bool SHIFT>
-cudaError_t launch_fwd16(const RowArgs& a, cudaStream_t s) {
+template <int LOGN, bool SHIFT, bool HALF>
+cudaError_t launch_fwd16_h(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
   const size_t smem = (size_t)N * sizeof(float4) + (size_t)2 * a.ld * sizeof(float2) +
                       (size_t)2 * a.taps_ld * sizeof(unsigned);
-  cudaError_t e = set_smem(stolt_fwd_rows16<LOGN, SHIFT>, smem_cap<LOGN>(true), attr);
+  cudaError_t e = set_smem(stolt_fwd_rows16<LOGN, SHIFT, HALF>, smem_cap<LOGN>(true), attr);
   if (e != cudaSuccess) return e;
-  stolt_fwd_rows16<LOGN, SHIFT><<<dim3(a.Lh, (a.batch + 1) / 2), N / 16, smem, s>>>(a);
+  stolt_fwd_rows16<LOGN, SHIFT, HALF><<<dim3(a.Lh, (a.batch + 1) / 2), N / 16, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int LOGN, bool SHIFT>
+cudaError_t launch_fwd16(const RowArgs& a, cudaStream_t s) {
+  return 2 * a.nt <= a.Nt ? launch_fwd16_h<LOGN, SHIFT, true>(a, s)
+                          : launch_fwd16_h<LOGN, SHIFT, false>(a, s);
 }
 
 template <int LOGN, bool SHIFT>

@@ -69,6 +69,40 @@ __device__ __forceinline__ void dft16(E* v) {
   }
 }
 
+// dft16 of inputs v[0..7] with v[8..15] = 0 (a zero-padded half): the first
+// stage's length-4 transforms have two zero inputs.
+template <int DIR, typename E>
+__device__ __forceinline__ void dft16_half(E* v) {
+  E y[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    E a0 = v[n2], a1 = v[n2 + 4], a2, a3;
+    dft4_half<DIR>(a0, a1, a2, a3);
+    y[4 * n2] = a0;
+    y[4 * n2 + 1] = a1;
+    y[4 * n2 + 2] = a2;
+    y[4 * n2 + 3] = a3;
+  }
+  y[5] = crot<DIR>(y[5], kCos8, kSin8);
+  y[6] = mul_eighth<DIR>(y[6]);
+  y[7] = crot<DIR>(y[7], kSin8, kCos8);
+  y[9] = mul_eighth<DIR>(y[9]);
+  y[10] = mul_quarter<DIR>(y[10]);
+  y[11] = mul_3eighth<DIR>(y[11]);
+  y[13] = crot<DIR>(y[13], kSin8, kCos8);
+  y[14] = mul_3eighth<DIR>(y[14]);
+  y[15] = crot<DIR>(y[15], -kCos8, -kSin8);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    E b0 = y[k1], b1 = y[4 + k1], b2 = y[8 + k1], b3 = y[12 + k1];
+    dft4<DIR>(b0, b1, b2, b3);
+    v[k1] = b0;
+    v[k1 + 4] = b1;
+    v[k1 + 8] = b2;
+    v[k1 + 12] = b3;
+  }
+}
+
 template <int DIR, int R, typename E>
 __device__ __forceinline__ void dft16_r(E* v) {
   if constexpr (R == 16) dft16<DIR>(v);
@@ -168,10 +202,12 @@ __device__ __forceinline__ void r16_pass_range(E* buf, const float2* __restrict_
   }
 }
 
-// First pass (radix 16, Ns = 1) from registers v[r] = x[tid + r N/16].
-template <int DIR, typename E>
+// First pass (radix 16, Ns = 1) from registers v[r] = x[tid + r N/16];
+// HALF: v[8..15] are zero (a row zero-padded to twice its length).
+template <int DIR, typename E, bool HALF = false>
 __device__ __forceinline__ void r16_first_pass(E* buf, E* v, int tid) {
-  dft16<DIR>(v);
+  if constexpr (HALF) dft16_half<DIR>(v);
+  else dft16<DIR>(v);
 #pragma unroll
   for (int r = 0; r < 16; ++r) buf[swz16<E>(tid * 16 + r)] = v[r];
   __syncthreads();

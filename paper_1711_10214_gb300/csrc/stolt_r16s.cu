@@ -74,7 +74,7 @@ __device__ __forceinline__ float2 adj_gather1(const float2* dsp, uint2 e, int j,
 // row, FFT it along tau, and accumulate the interpolated bins of the Stolt
 // map (taps from the tap word of |k|) times the asymptote phase in registers;
 // finally weight by W(w) / (Nt Nx), inverse FFT, keep nt samples.
-template <int LOGN, bool SHIFT>
+template <int LOGN, bool SHIFT, bool HALF>
 __global__ void __launch_bounds__((1 << LOGN) / 16, r16s_minb_fwd<LOGN>())
 stolt_fwd_rows16s(RowArgs a) {
   constexpr int N = 1 << LOGN, T = N / 16;
@@ -106,14 +106,14 @@ stolt_fwd_rows16s(RowArgs a) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int i = tid + r * T;
-      v[r] = i < a.nt ? stage[i] : make_float2(0.f, 0.f);
+      v[r] = (!(HALF && r >= 8) && i < a.nt) ? stage[i] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     if (p + 1 < a.P) {
       stage_row1(stage, xr + (long long)(p + 1) * a.x_panel, a.ld, tid, T);
       cp_async_commit();
     }
-    r16_first_pass<-1>(buf, v, tid);
+    r16_first_pass<-1, float2, HALF>(buf, v, tid);
     r16_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw16, tid);
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
@@ -219,15 +219,22 @@ stolt_adj_rows16s(RowArgs a) {
   }
 }
 
-template <int LOGN, bool SHIFT>
-cudaError_t launch_fwd16s(const RowArgs& a, cudaStream_t s) {
+template <int LOGN, bool SHIFT, bool HALF>
+cudaError_t launch_fwd16s_h(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
   const size_t smem = (size_t)(N + a.ld) * sizeof(float2);
-  cudaError_t e = set_smem(stolt_fwd_rows16s<LOGN, SHIFT>, (size_t)2 * N * sizeof(float2), attr);
+  cudaError_t e = set_smem(stolt_fwd_rows16s<LOGN, SHIFT, HALF>, (size_t)2 * N * sizeof(float2),
+                           attr);
   if (e != cudaSuccess) return e;
-  stolt_fwd_rows16s<LOGN, SHIFT><<<dim3(a.batch, a.Lh), N / 16, smem, s>>>(a);
+  stolt_fwd_rows16s<LOGN, SHIFT, HALF><<<dim3(a.batch, a.Lh), N / 16, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int LOGN, bool SHIFT>
+cudaError_t launch_fwd16s(const RowArgs& a, cudaStream_t s) {
+  return 2 * a.nt <= a.Nt ? launch_fwd16s_h<LOGN, SHIFT, true>(a, s)
+                          : launch_fwd16s_h<LOGN, SHIFT, false>(a, s);
 }
 
 template <int LOGN, bool SHIFT>
