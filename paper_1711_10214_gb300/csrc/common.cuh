@@ -229,7 +229,10 @@ __device__ __forceinline__ float2 base_twiddle(const float2* __restrict__ tw, in
 // One in-place Stockham pass on a single shared row of N float2, executed by
 // T = N/8 threads (each handles 8 values: one radix-8, two radix-4 or four
 // radix-2 butterflies).  Reads everything, barrier, writes, barrier.
-template <int DIR, int N, int R, typename E>
+// PLAIN_OUT writes the (natural-order) outputs without the swizzle: meant for
+// the last pass, whose butterfly jb < Ns writes elements jb + r Ns, i.e.
+// consecutive elements across the lanes.
+template <int DIR, int N, int R, typename E, bool PLAIN_OUT = false>
 __device__ __forceinline__ void row_pass(E* buf, int Ns, const float2* __restrict__ tw,
                                          int tw_off, int tid) {
   constexpr int T = N / 8;
@@ -250,20 +253,26 @@ __device__ __forceinline__ void row_pass(E* buf, int Ns, const float2* __restric
     dft_r<DIR, R>(&v[q * R]);
     const int base = (jb - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[swz_e<E>(base + r * Ns)] = v[q * R + r];
+    for (int r = 0; r < R; ++r) {
+      const int o = base + r * Ns;
+      buf[PLAIN_OUT ? o : swz_e<E>(o)] = v[q * R + r];
+    }
   }
   __syncthreads();
 }
 
-// Passes Q0 <= q < Q1 of a length-2^LOGN transform, in place in shared memory.
-template <int DIR, int LOGN, int Q0, int Q1, typename E>
+// Passes Q0 <= q < Q1 of a length-2^LOGN transform, in place in shared memory;
+// LAST_PLAIN: pass Q1 - 1 is the transform's last and leaves its natural-order
+// output unswizzled.
+template <int DIR, int LOGN, int Q0, int Q1, typename E, bool LAST_PLAIN = false>
 __device__ __forceinline__ void row_pass_range(E* buf, const float2* __restrict__ tw,
                                                int tid) {
   using S = Sched<LOGN>;
   if constexpr (Q0 < Q1) {
     constexpr int R = S::radix(Q0);
-    row_pass<DIR, S::N, R, E>(buf, S::ns(Q0), tw, S::tw_off(Q0), tid);
-    row_pass_range<DIR, LOGN, Q0 + 1, Q1>(buf, tw, tid);
+    constexpr bool plain = LAST_PLAIN && Q0 + 1 == Q1 && Q1 == S::NPASS;
+    row_pass<DIR, S::N, R, E, plain>(buf, S::ns(Q0), tw, S::tw_off(Q0), tid);
+    row_pass_range<DIR, LOGN, Q0 + 1, Q1, E, LAST_PLAIN>(buf, tw, tid);
   }
 }
 

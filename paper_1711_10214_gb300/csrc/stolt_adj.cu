@@ -67,11 +67,11 @@ stolt_adj_rows(RowArgs a) {
   float4 v[8];
   load_pair<N>(v, yA, hasB ? yA + a.y_batch : nullptr, a.nt, tid);
   row_first_pass<-1, N>(buf, v, tid);
-  row_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw, tid);
+  row_pass_range<-1, LOGN, 1, S::NPASS, float4, true>(buf, a.tw, tid);
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int k = tid + T * s;
-    dsp[swz4(k)] = cscale(buf[swz4(k)], __ldg(a.wt + k));
+    dsp[k] = cscale(buf[k], __ldg(a.wt + k));   // natural order, unswizzled
   }
 
   float2* xA = a.Xw + (long long)b0 * a.x_batch + (long long)l * a.ld;
@@ -87,9 +87,9 @@ stolt_adj_rows(RowArgs a) {
     float4 accs[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s)
-      accs[s] = mapped ? adj_gather_bin<N, 3, SHIFT>(dsp, stab, tid + T * s, phj)
+      accs[s] = mapped ? adj_gather_bin<N, 0, SHIFT>(dsp, stab, tid + T * s, phj)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tid == 0 && mapped) accs[0] = adj_gather_bin0_mirror<N, 3, SHIFT>(dsp, stab, phj, accs[0]);
+    if (tid == 0 && mapped) accs[0] = adj_gather_bin0_mirror<N, 0, SHIFT>(dsp, stab, phj, accs[0]);
     // first pass from the registers (its barrier also ends every thread's
     // reads of the source-table row, which is then restaged)
     row_first_pass<+1, N>(buf, accs, tid);

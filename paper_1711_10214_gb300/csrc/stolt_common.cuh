@@ -91,10 +91,12 @@ __device__ __forceinline__ void stage_tab(uint2* dst, const uint2* src, int n, i
 }
 
 // Swizzle of a shared float4 row: XOR the 16-byte bank group (low 3 bits)
-// with bits SW..SW+2 of the index (SW = 3: swz4 of common.cuh).
+// with bits SW..SW+2 of the index (SW = 3: swz4 of common.cuh); SW = 0: no
+// swizzle (a row written in natural order by consecutive lanes).
 template <int SW>
 __device__ __forceinline__ int swz_g(int i) {
-  return i ^ ((i >> SW) & 7);
+  if constexpr (SW == 0) return i;
+  else return i ^ ((i >> SW) & 7);
 }
 
 // One output bin j of the transposed Stolt map, gather form: the secondary

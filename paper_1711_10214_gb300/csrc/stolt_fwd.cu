@@ -97,15 +97,15 @@ stolt_fwd_rows(RowArgs a) {
       for (int s = 0; s < 8; ++s) ph[s] = __ldg(a.phase + (long long)jt * N + tid + T * s);
     }
     row_first_pass<-1, N, float4, HALF>(buf, v, tid);
-    row_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw, tid);
+    row_pass_range<-1, LOGN, 1, S::NPASS, float4, true>(buf, a.tw, tid);   // natural order, unswizzled
 
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int k = tid + T * s;
       const Tap t = tap_decode<N>(k, stap[kabs_of<N>(k)]);
       if (t.valid) {
-        float4 vk = cscale(buf[swz4(t.i0)], t.w0);
-        vk = cfma(t.w1, buf[swz4(t.i1)], vk);
+        float4 vk = cscale(buf[t.i0], t.w0);
+        vk = cfma(t.w1, buf[t.i1], vk);
         if (SHIFT) vk = cmul(vk, ph[s]);
         acc[s] = cadd(acc[s], vk);
       }

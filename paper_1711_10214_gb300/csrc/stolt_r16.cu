@@ -86,15 +86,15 @@ stolt_fwd_rows16(RowArgs a) {
       cp_async_commit();
     }
     r16_first_pass<-1, float4, HALF>(buf, v, tid);
-    r16_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw16, tid);
+    r16_pass_range<-1, LOGN, 1, S::NPASS, float4, true>(buf, a.tw16, tid);   // natural, unswizzled
 
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
       const int k = tid + T * s;
       const Tap t = tap_decode<N>(k, stap[kabs_of<N>(k)]);
       if (t.valid) {
-        float4 vk = cscale(buf[swz16<float4>(t.i0)], t.w0);
-        vk = cfma(t.w1, buf[swz16<float4>(t.i1)], vk);
+        float4 vk = cscale(buf[t.i0], t.w0);
+        vk = cfma(t.w1, buf[t.i1], vk);
         if (SHIFT) vk = cmul(vk, __ldg(a.phase + (long long)jt * N + k));
         acc[s] = cadd(acc[s], vk);
       }
@@ -144,11 +144,11 @@ stolt_adj_rows16(RowArgs a) {
     }
     r16_first_pass<-1>(buf, v, tid);
   }
-  r16_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw16, tid);
+  r16_pass_range<-1, LOGN, 1, S::NPASS, float4, true>(buf, a.tw16, tid);
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
     const int k = tid + T * s;
-    dsp[swz16<float4>(k)] = cscale(buf[swz16<float4>(k)], __ldg(a.wt + k));
+    dsp[k] = cscale(buf[k], __ldg(a.wt + k));   // natural order, unswizzled
   }
 
   float2* xA = a.Xw + (long long)b0 * a.x_batch + (long long)l * a.ld;
@@ -162,9 +162,9 @@ stolt_adj_rows16(RowArgs a) {
     float4 accs[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s)
-      accs[s] = mapped ? adj_gather_bin<N, 4, SHIFT>(dsp, stab, tid + T * s, phj)
+      accs[s] = mapped ? adj_gather_bin<N, 0, SHIFT>(dsp, stab, tid + T * s, phj)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tid == 0 && mapped) accs[0] = adj_gather_bin0_mirror<N, 4, SHIFT>(dsp, stab, phj, accs[0]);
+    if (tid == 0 && mapped) accs[0] = adj_gather_bin0_mirror<N, 0, SHIFT>(dsp, stab, phj, accs[0]);
     // its barrier also ends every thread's reads of the source-table row
     r16_first_pass<+1>(buf, accs, tid);
     if (p + 1 < a.P) {

@@ -167,8 +167,8 @@ __device__ __forceinline__ int swz16(int i) {
 }
 
 // One in-place Stockham pass, T = N/16 threads, each with 16 / R butterflies
-// of radix R.
-template <int DIR, int N, int R, typename E>
+// of radix R; PLAIN_OUT as in row_pass (common.cuh).
+template <int DIR, int N, int R, typename E, bool PLAIN_OUT = false>
 __device__ __forceinline__ void r16_pass(E* buf, int Ns, const float2* __restrict__ tw, int off,
                                          int tid) {
   constexpr int T = N / 16, NB = 16 / R;
@@ -188,17 +188,23 @@ __device__ __forceinline__ void r16_pass(E* buf, int Ns, const float2* __restric
     dft16_r<DIR, R>(&v[q * R]);
     const int base = (jb - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[swz16<E>(base + r * Ns)] = v[q * R + r];
+    for (int r = 0; r < R; ++r) {
+      const int o = base + r * Ns;
+      buf[PLAIN_OUT ? o : swz16<E>(o)] = v[q * R + r];
+    }
   }
   __syncthreads();
 }
 
-template <int DIR, int LOGN, int Q0, int Q1, typename E>
+// LAST_PLAIN: pass Q1 - 1 is the transform's last and leaves its
+// natural-order output unswizzled.
+template <int DIR, int LOGN, int Q0, int Q1, typename E, bool LAST_PLAIN = false>
 __device__ __forceinline__ void r16_pass_range(E* buf, const float2* __restrict__ tw, int tid) {
   using S = Sched16<LOGN>;
   if constexpr (Q0 < Q1) {
-    r16_pass<DIR, S::N, S::radix(Q0)>(buf, S::ns(Q0), tw, S::tw_off(Q0), tid);
-    r16_pass_range<DIR, LOGN, Q0 + 1, Q1>(buf, tw, tid);
+    constexpr bool plain = LAST_PLAIN && Q0 + 1 == Q1 && Q1 == S::NPASS;
+    r16_pass<DIR, S::N, S::radix(Q0), E, plain>(buf, S::ns(Q0), tw, S::tw_off(Q0), tid);
+    r16_pass_range<DIR, LOGN, Q0 + 1, Q1, E, LAST_PLAIN>(buf, tw, tid);
   }
 }
 

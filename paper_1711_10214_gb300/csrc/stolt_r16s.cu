@@ -57,13 +57,13 @@ __device__ __forceinline__ float2 adj_gather1(const float2* dsp, uint2 e, int j,
   const int kB = (int)(e.x >> 20);
   if (e.y & (1u << 21)) {
     const int kn = pos ? kB - 1 : N - kB + 1;
-    float2 d = dsp[swz16<float2>(kn)];
+    float2 d = dsp[kn];
     if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
     acc = cscale(d, (float)(e.y & 0xfffffu) * (1.0f / 1048576.0f));
   }
   if (e.y & (1u << 20)) {
     const int kn = pos ? kB : N - kB;
-    float2 d = dsp[swz16<float2>(kn)];
+    float2 d = dsp[kn];
     if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
     acc = cfma(1.f - (float)(e.x & 0xfffffu) * (1.0f / 1048576.0f), d, acc);
   }
@@ -114,14 +114,14 @@ stolt_fwd_rows16s(RowArgs a) {
       cp_async_commit();
     }
     r16_first_pass<-1, float2, HALF>(buf, v, tid);
-    r16_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw16, tid);
+    r16_pass_range<-1, LOGN, 1, S::NPASS, float2, true>(buf, a.tw16, tid);   // natural, unswizzled
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
       const int k = tid + T * s;
       const Tap t = tap_decode<N>(k, tw[s]);
       if (t.valid) {
-        float2 vk = cscale(buf[swz16<float2>(t.i0)], t.w0);
-        vk = cfma(t.w1, buf[swz16<float2>(t.i1)], vk);
+        float2 vk = cscale(buf[t.i0], t.w0);
+        vk = cfma(t.w1, buf[t.i1], vk);
         if (SHIFT) vk = cmul(vk, __ldg(a.phase + (long long)jt * N + k));
         acc[s] = cadd(acc[s], vk);
       }
@@ -172,11 +172,11 @@ stolt_adj_rows16s(RowArgs a) {
     }
     r16_first_pass<-1>(buf, v, tid);
   }
-  r16_pass_range<-1, LOGN, 1, S::NPASS>(buf, a.tw16, tid);
+  r16_pass_range<-1, LOGN, 1, S::NPASS, float2, true>(buf, a.tw16, tid);
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
     const int k = tid + T * s;
-    dsp[swz16<float2>(k)] = cscale(buf[swz16<float2>(k)], __ldg(a.wt + k));
+    dsp[k] = cscale(buf[k], __ldg(a.wt + k));   // natural order, unswizzled
   }
 
   float2* xr = a.Xw + (long long)b * a.x_batch + (long long)l * a.ld;
@@ -202,7 +202,7 @@ stolt_adj_rows16s(RowArgs a) {
       if (tid == 0 && (ent[0].y & (1u << 20))) {
         // bin 0 also takes the primary tap of -kB (w = 0 lies on both sides)
         const int kn = N - (int)(ent[0].x >> 20);
-        float2 d = dsp[swz16<float2>(kn)];
+        float2 d = dsp[kn];
         if (SHIFT) d = cmul(d, cconj(__ldg(phj + kn)));
         accs[0] = cfma(1.f - (float)(ent[0].x & 0xfffffu) * (1.0f / 1048576.0f), d, accs[0]);
       }
