@@ -87,7 +87,7 @@ stolt_adj_rows(RowArgs a) {
     float4 accs[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s)
-      accs[s] = mapped ? adj_gather_bin<N, 0, SHIFT>(dsp, stab, tid + T * s, phj)
+      accs[s] = mapped ? adj_gather_bin<N, 0, SHIFT>(dsp, stab, tid + T * s, phj, s < 4)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid == 0 && mapped) accs[0] = adj_gather_bin0_mirror<N, 0, SHIFT>(dsp, stab, phj, accs[0]);
     // first pass from the registers (its barrier also ends every thread's

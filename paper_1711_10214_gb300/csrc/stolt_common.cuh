@@ -69,6 +69,29 @@ __device__ __forceinline__ int kabs_of(int k) {
   return k <= N / 2 ? k : N - k;
 }
 
+// tap_decode for a bin whose side of the spectrum the caller knows: pos means
+// k < N/2; otherwise k >= N/2 (the w-Nyquist bin k = N/2 is unmapped).  The
+// row kernels' bins k = tid + T s lie on the positive side exactly for the
+// first half of the slots s, so after unrolling `pos` is a constant and the
+// side selection and the table index fold away.
+template <int N>
+__device__ __forceinline__ Tap tap_decode_side(int k, unsigned w, bool pos) {
+  Tap t;
+  t.valid = (pos || k != N / 2) && (w != kTapInvalid);
+  const int k0 = (int)(w >> 20);
+  const float f = (float)(w & 0xfffffu) * (1.0f / 1048576.0f);
+  if (pos) {
+    t.i0 = k0;
+    t.i1 = k0 + 1;
+  } else {
+    t.i0 = (N - k0) & (N - 1);
+    t.i1 = (N - k0 - 1) & (N - 1);
+  }
+  t.w0 = 1.f - f;
+  t.w1 = (t.i1 == N / 2) ? 0.f : f;
+  return t;
+}
+
 // Stage the rows of gathers A and B (B may be absent) of one panel: ld
 // complex values each (ld is a multiple of 4, rows are 32-byte aligned).
 __device__ __forceinline__ void stage_rows(float2* stage, const float2* rowA, const float2* rowB,
@@ -105,13 +128,14 @@ __device__ __forceinline__ int swz_g(int i) {
 // on j's side of the spectrum; the w-Nyquist bin takes nothing.  dsp holds
 // the weighted data spectrum; with SHIFT each source is multiplied by the
 // conjugate asymptote phase of its own bin.
+// pos: j < N/2 when the caller knows the side (see tap_decode_side), else
+// j >= N/2.
 template <int N, int SW, bool SHIFT>
 __device__ __forceinline__ float4 adj_gather_bin(const float4* dsp, const uint2* stab, int j,
-                                                 const float2* __restrict__ phj) {
+                                                 const float2* __restrict__ phj, bool pos) {
   constexpr int H = N / 2;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (j == H) return acc;
-  const bool pos = j < H;
+  if (!pos && j == H) return acc;
   const uint2 e = stab[pos ? j : N - j];
   const int kB = (int)(e.x >> 20);
   if (e.y & (1u << 21)) {

@@ -102,7 +102,8 @@ stolt_fwd_rows(RowArgs a) {
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int k = tid + T * s;
-      const Tap t = tap_decode<N>(k, stap[kabs_of<N>(k)]);
+      const bool pos = s < 4;                      // k < N/2 exactly for the first half of s
+      const Tap t = tap_decode_side<N>(k, stap[pos ? k : N - k], pos);
       if (t.valid) {
         float4 vk = cscale(buf[t.i0], t.w0);
         vk = cfma(t.w1, buf[t.i1], vk);

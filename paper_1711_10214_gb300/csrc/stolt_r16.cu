@@ -91,7 +91,8 @@ stolt_fwd_rows16(RowArgs a) {
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
       const int k = tid + T * s;
-      const Tap t = tap_decode<N>(k, stap[kabs_of<N>(k)]);
+      const bool pos = s < 8;                      // k < N/2 exactly for the first half of s
+      const Tap t = tap_decode_side<N>(k, stap[pos ? k : N - k], pos);
       if (t.valid) {
         float4 vk = cscale(buf[t.i0], t.w0);
         vk = cfma(t.w1, buf[t.i1], vk);
@@ -162,7 +163,7 @@ stolt_adj_rows16(RowArgs a) {
     float4 accs[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s)
-      accs[s] = mapped ? adj_gather_bin<N, 0, SHIFT>(dsp, stab, tid + T * s, phj)
+      accs[s] = mapped ? adj_gather_bin<N, 0, SHIFT>(dsp, stab, tid + T * s, phj, s < 8)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid == 0 && mapped) accs[0] = adj_gather_bin0_mirror<N, 0, SHIFT>(dsp, stab, phj, accs[0]);
     // its barrier also ends every thread's reads of the source-table row

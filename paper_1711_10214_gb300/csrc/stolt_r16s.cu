@@ -118,7 +118,7 @@ stolt_fwd_rows16s(RowArgs a) {
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
       const int k = tid + T * s;
-      const Tap t = tap_decode<N>(k, tw[s]);
+      const Tap t = tap_decode_side<N>(k, tw[s], s < 8);
       if (t.valid) {
         float2 vk = cscale(buf[t.i0], t.w0);
         vk = cfma(t.w1, buf[t.i1], vk);
