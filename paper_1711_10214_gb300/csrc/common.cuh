@@ -202,13 +202,6 @@ struct Sched {
     return o;
   }
   static constexpr int TW_LEN = tw_off(NPASS);
-  // offset of pass q's power table (R - 1 rows of Ns twiddles, see
-  // twiddle_r_tab) inside the per-length power table of the row kernels
-  __host__ __device__ static constexpr int tp_off(int q) {
-    int o = 0;
-    for (int i = 0; i < q; ++i) o += (radix(i) - 1) * ns(i);
-    return o;
-  }
 };
 
 // Shared-memory swizzles for one length-N row: XOR the column bits of a
@@ -230,21 +223,6 @@ __device__ __forceinline__ float2 base_twiddle(const float2* __restrict__ tw, in
   float2 w = __ldg(tw + off + k);
   if (DIR > 0) w.y = -w.y;
   return w;
-}
-
-// v[r] *= w^r, r = 1..R-1, the powers read from a pass's power table: row
-// r - 1 holds exp(-2 pi i r k / (Ns R)) for k < Ns (built in FP64 on the host;
-// conjugated for the synthesis direction).  Consecutive butterflies read
-// consecutive entries of each row.
-template <int R, int DIR, typename E>
-__device__ __forceinline__ void twiddle_r_tab(E* v, const float2* __restrict__ tp, int off, int Ns,
-                                              int k) {
-#pragma unroll
-  for (int r = 1; r < R; ++r) {
-    float2 w = __ldg(tp + off + (r - 1) * Ns + k);
-    if (DIR > 0) w.y = -w.y;
-    v[r] = cmul(v[r], w);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -271,7 +249,7 @@ __device__ __forceinline__ void row_pass(E* buf, int Ns, const float2* __restric
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
     const int k = jb & (Ns - 1);
-    if (Ns > 1) twiddle_r_tab<R, DIR>(&v[q * R], tw, tw_off, Ns, k);
+    if (Ns > 1) twiddle_r<R>(&v[q * R], base_twiddle<DIR>(tw, tw_off, k));
     dft_r<DIR, R>(&v[q * R]);
     const int base = (jb - k) * R + k;
 #pragma unroll
@@ -293,7 +271,7 @@ __device__ __forceinline__ void row_pass_range(E* buf, const float2* __restrict_
   if constexpr (Q0 < Q1) {
     constexpr int R = S::radix(Q0);
     constexpr bool plain = LAST_PLAIN && Q0 + 1 == Q1 && Q1 == S::NPASS;
-    row_pass<DIR, S::N, R, E, plain>(buf, S::ns(Q0), tw, S::tp_off(Q0), tid);
+    row_pass<DIR, S::N, R, E, plain>(buf, S::ns(Q0), tw, S::tw_off(Q0), tid);
     row_pass_range<DIR, LOGN, Q0 + 1, Q1, E, LAST_PLAIN>(buf, tw, tid);
   }
 }
@@ -330,7 +308,7 @@ __device__ __forceinline__ void row_last_pass_global(E* buf, const float2* __res
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
-    if (Ns > 1) twiddle_r_tab<R, DIR>(&v[q * R], tw, S::tp_off(Q), Ns, jb);
+    if (Ns > 1) twiddle_r<R>(&v[q * R], base_twiddle<DIR>(tw, S::tw_off(Q), jb));
     dft_r<DIR, R>(&v[q * R]);
 #pragma unroll
     for (int r = 0; r < R; ++r) {

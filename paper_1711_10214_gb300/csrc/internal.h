@@ -61,7 +61,7 @@ struct RowArgs {
   float2* Yw = nullptr;
   int nt = 0, ld = 0, Lh = 0, P = 0, nv = 0, nt0 = 0, Nt = 0;
   long long x_batch = 0, x_panel = 0, y_batch = 0;
-  const float2* tw = nullptr;      // twiddle power table of the radix-8 schedule (Nt - 1 entries)
+  const float2* tw = nullptr;      // base twiddles of length Nt
   const float2* tw16 = nullptr;    // the same for the radix-16 schedule (stolt_r16.cu), or null
   const float* wt = nullptr;       // [Nt] spectral weight W(w)/(Nt Nx), 0 at unmapped bins
   const int* kmin = nullptr;       // [nv][Lh] first mapped |k| (host FP64 cone rule)
@@ -135,11 +135,6 @@ cudaError_t launch_irr_cg_r(float* r, const float* q, long long n, const float4*
 // radix (lr = 3 for the radix-8 kernels, 4 for the radix-16 row kernels).
 int twiddle_table_len(int logn, int lr = 3);
 void build_twiddle_table(int logn, float2* out, int lr = 3);
-// Power tables of the row kernels' passes: for each pass (radix R after Ns
-// earlier points) R - 1 rows of Ns entries, row r - 1 holding
-// exp(-2 pi i r k / (Ns R)), k < Ns (FP64, rounded once).  Length Nt - 1.
-int twiddle_power_len(int logn, int lr = 3);
-void build_twiddle_powers(int logn, float2* out, int lr = 3);
 
 void set_error(const char* fmt, ...);
 
@@ -189,8 +184,8 @@ struct ashrt_plan {
   int rows_minb = 3;         // row-kernel variant 1..8 (autotuned; see ashrt_plan_autotune)
   int xfft_cols = 16;
   // device tables
-  float2* tw_t = nullptr;    // row kernels' twiddle power table, radix-8 schedule
-  float2* tw_t16 = nullptr;  // the same, radix-16 schedule (rows16_supported), else null
+  float2* tw_t = nullptr;
+  float2* tw_t16 = nullptr;  // radix-16 schedule of length Nt (rows16_supported), else null
   float2* tw_x = nullptr;
   float* wt = nullptr;
   int* kmin = nullptr;

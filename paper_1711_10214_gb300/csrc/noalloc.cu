@@ -102,7 +102,7 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
   }
 
   // scratch layout, every piece 256-byte aligned
-  const size_t tw_t_len = twiddle_power_len(logNt), tw_x_len = twiddle_table_len(logNx);
+  const size_t tw_t_len = twiddle_table_len(logNt), tw_x_len = twiddle_table_len(logNx);
   size_t off = 0;
   const size_t o_twt = off;   off = align256(off + tw_t_len * sizeof(float2));
   const size_t o_twx = off;   off = align256(off + tw_x_len * sizeof(float2));
@@ -137,7 +137,7 @@ extern "C" ashrt_status ashrt_forward_static(int nt, int nx, double dt, double d
 
   // host tables (the same builders ashrt_plan_create uses)
   std::vector<float2> twt(tw_t_len), twx(tw_x_len);
-  build_twiddle_powers(logNt, twt.data());   // the row kernel's power table
+  build_twiddle_table(logNt, twt.data());
   build_twiddle_table(logNx, twx.data());
   std::vector<float> wt(Nt);
   for (int k = 0; k < Nt; ++k) {

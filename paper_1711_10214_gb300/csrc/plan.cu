@@ -57,34 +57,6 @@ void build_twiddle_table(int logn, float2* out, int lr) {
   }
 }
 
-int twiddle_power_len(int logn, int lr) {
-  int nf = logn / lr, rl = 1 << (logn % lr), np = nf + (rl > 1 ? 1 : 0);
-  int len = 0, ns = 1;
-  for (int q = 0; q < np; ++q) {
-    const int R = q < nf ? (1 << lr) : rl;
-    len += (R - 1) * ns;
-    ns *= R;
-  }
-  return len;
-}
-
-void build_twiddle_powers(int logn, float2* out, int lr) {
-  int nf = logn / lr, rl = 1 << (logn % lr), np = nf + (rl > 1 ? 1 : 0);
-  int off = 0, ns = 1;
-  for (int q = 0; q < np; ++q) {
-    const int R = q < nf ? (1 << lr) : rl;
-    for (int r = 1; r < R; ++r)
-      for (int k = 0; k < ns; ++k) {
-        // the phase r k / (ns R) reduced exactly in integers before scaling
-        const long long m = ((long long)r * k) % ((long long)ns * R);
-        const double ang = -2.0 * M_PI * (double)m / (double)(ns * R);
-        out[off + (r - 1) * ns + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-      }
-    off += (R - 1) * ns;
-    ns *= R;
-  }
-}
-
 // Cone table and Stolt taps for every (velocity, l) row, in FP64: the same
 // expressions as the FP64 reference, a = ((v*l)*Nt)*dt/(Nx*dx), mapped iff
 // k*k > a*a, u = sqrt(k^2 - a^2).
@@ -544,9 +516,8 @@ static ashrt_status plan_create_impl(ashrt_plan** out, int nt, int nx, double dt
     }
   }
   p->shift = shift;
-  // the row kernels' passes read power tables, the trace-axis passes base twiddles
-  std::vector<float2> twt(twiddle_power_len(p->logNt)), twx(twiddle_table_len(p->logNx));
-  build_twiddle_powers(p->logNt, twt.data());
+  std::vector<float2> twt(twiddle_table_len(p->logNt)), twx(twiddle_table_len(p->logNx));
+  build_twiddle_table(p->logNt, twt.data());
   build_twiddle_table(p->logNx, twx.data());
 
   size_t total = 0;
@@ -557,8 +528,8 @@ static ashrt_status plan_create_impl(ashrt_plan** out, int nt, int nx, double dt
   chk(upload(&p->tw_t, twt, &total));
   chk(upload(&p->tw_x, twx, &total));
   if (rows16_supported(p->logNt)) {
-    std::vector<float2> tw16(twiddle_power_len(p->logNt, 4));
-    build_twiddle_powers(p->logNt, tw16.data(), 4);
+    std::vector<float2> tw16(twiddle_table_len(p->logNt, 4));
+    build_twiddle_table(p->logNt, tw16.data(), 4);
     chk(upload(&p->tw_t16, tw16, &total));
     p->rows_minb = 4;        // radix-16 forward, radix-8 adjoint: the faster pair
   }

@@ -109,6 +109,36 @@ __device__ __forceinline__ void dft16_r(E* v) {
   else dft_r<DIR, R>(v);
 }
 
+// v[r] *= w^r, r = 1..R-1: powers by products of at most four factors,
+// each used for r and r + 8 as soon as it is formed (few live registers).
+template <int R, typename E>
+__device__ __forceinline__ void twiddle16_r(E* v, float2 w) {
+  if constexpr (R == 16) {
+    const float2 w2 = cmul(w, w), w4 = cmul(w2, w2), w8 = cmul(w4, w4);
+    const float2 w3 = cmul(w2, w);
+    v[8] = cmul(v[8], w8);
+    v[1] = cmul(v[1], w);
+    v[9] = cmul(v[9], cmul(w8, w));
+    v[2] = cmul(v[2], w2);
+    v[10] = cmul(v[10], cmul(w8, w2));
+    v[3] = cmul(v[3], w3);
+    v[11] = cmul(v[11], cmul(w8, w3));
+    v[4] = cmul(v[4], w4);
+    v[12] = cmul(v[12], cmul(w8, w4));
+    const float2 w5 = cmul(w4, w);
+    v[5] = cmul(v[5], w5);
+    v[13] = cmul(v[13], cmul(w8, w5));
+    const float2 w6 = cmul(w4, w2);
+    v[6] = cmul(v[6], w6);
+    v[14] = cmul(v[14], cmul(w8, w6));
+    const float2 w7 = cmul(w4, w3);
+    v[7] = cmul(v[7], w7);
+    v[15] = cmul(v[15], cmul(w8, w7));
+  } else {
+    twiddle_r<R>(v, w);
+  }
+}
+
 // Radix schedule of a length 2^LOGN transform: radix 16 while four or more
 // factors of two remain, then one radix 2, 4 or 8 pass.
 template <int LOGN>
@@ -126,12 +156,6 @@ struct Sched16 {
   __host__ __device__ static constexpr int tw_off(int q) {
     int o = 0;
     for (int i = 0; i < q; ++i) o += ns(i);
-    return o;
-  }
-  // offset of pass q's power table (see twiddle_r_tab in common.cuh)
-  __host__ __device__ static constexpr int tp_off(int q) {
-    int o = 0;
-    for (int i = 0; i < q; ++i) o += (radix(i) - 1) * ns(i);
     return o;
   }
 };
@@ -160,7 +184,7 @@ __device__ __forceinline__ void r16_pass(E* buf, int Ns, const float2* __restric
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
     const int k = jb & (Ns - 1);
-    if (Ns > 1) twiddle_r_tab<R, DIR>(&v[q * R], tw, off, Ns, k);
+    if (Ns > 1) twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, off, k));
     dft16_r<DIR, R>(&v[q * R]);
     const int base = (jb - k) * R + k;
 #pragma unroll
@@ -179,7 +203,7 @@ __device__ __forceinline__ void r16_pass_range(E* buf, const float2* __restrict_
   using S = Sched16<LOGN>;
   if constexpr (Q0 < Q1) {
     constexpr bool plain = LAST_PLAIN && Q0 + 1 == Q1 && Q1 == S::NPASS;
-    r16_pass<DIR, S::N, S::radix(Q0), E, plain>(buf, S::ns(Q0), tw, S::tp_off(Q0), tid);
+    r16_pass<DIR, S::N, S::radix(Q0), E, plain>(buf, S::ns(Q0), tw, S::tw_off(Q0), tid);
     r16_pass_range<DIR, LOGN, Q0 + 1, Q1, E, LAST_PLAIN>(buf, tw, tid);
   }
 }
@@ -215,7 +239,7 @@ __device__ __forceinline__ void r16_last_pass_global(const E* buf, const float2*
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
-    twiddle_r_tab<R, DIR>(&v[q * R], tw, S::tp_off(Q), Ns, jb);
+    twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, S::tw_off(Q), jb));
     dft16_r<DIR, R>(&v[q * R]);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
