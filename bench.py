@@ -66,10 +66,10 @@ def _args():
                     help="gathers per call (the deblend workload is 64; smaller batches are "
                          "for profiling captures)")
     ap.add_argument("--variant", type=int, default=0,
-                    help="deblend mode: row-kernel variant 1..5 instead of the autotuner's "
+                    help="deblend mode: row-kernel variant 1..8 instead of the autotuner's "
                          "choice (profiling captures skip the autotuner's launches this way)")
     ap.add_argument("--rows-variant", type=int, default=0,
-                    help="ops mode: row-kernel variant 1..5 (0: the plan's default; see "
+                    help="ops mode: row-kernel variant 1..8 (0: the plan's default; see "
                          "ashrt_plan_set_variant)")
     return ap.parse_args()
 
@@ -136,12 +136,13 @@ def source_hash(kernel):
     return h.hexdigest()[:12]
 
 
-def measured_traffic(kernel, gathers):
+def measured_traffic(kernel, gathers, variant=(4, 16)):
     """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
     of `kernel` over `gathers` gathers, scaled from the committed ncu capture
     in profiles/dram_traffic.md (rows: | kernel | gathers per launch | bytes
-    per launch | source hash | ...).  None when there is no capture of the
-    kernel's current sources."""
+    per launch | source hash | variant | ...), the variant being the plan's
+    rows_minb/xfft_cols.  None when there is no capture of the kernel's
+    current sources in the variant that ran."""
     try:
         with open(TRAFFIC_FILE) as f:
             rows = [ln.split("|")[1:-1] for ln in f if ln.startswith("| ")]
@@ -150,7 +151,7 @@ def measured_traffic(kernel, gathers):
     want = source_hash(kernel)
     for r in rows:
         r = [x.strip() for x in r]
-        if len(r) >= 4 and r[0] == kernel and r[3] == want:
+        if len(r) >= 5 and r[0] == kernel and r[3] == want and r[4] == "%d/%d" % tuple(variant):
             try:
                 return float(r[2]) / float(r[1]) * gathers, want
             except ValueError:
@@ -493,7 +494,7 @@ def run_ours(args):
     else:
         flops = (NV + 1) * NT * 0.5 * _fft_flops(512) * B
     achieved = flops / per_launch_s / 1e12
-    traffic, src_hash = measured_traffic(dom, B)
+    traffic, src_hash = measured_traffic(dom, B, variant)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,

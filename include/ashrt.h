@@ -338,8 +338,9 @@ ashrt_status ashrt_sort_gathers(const float* src_dev, int n0, int n1, int nt, fl
  * staged), 7: that forward with the radix-8 pair adjoint, 8: the radix-16
  * pair forward with that adjoint; the default is 4 where it applies, else 3)
  * and the trace-axis FFT column tile (16 or 8 columns for Nx <= 512) -- and
- * keeps
- * the fastest in the plan.  With cache_path (a JSON-lines file, one object per
+ * keeps the fastest in the plan; the plan's current choice is timed first and
+ * another one replaces it only when it is more than 2% faster, so variants
+ * within timing noise of each other do not flip from run to run.  With cache_path (a JSON-lines file, one object per
  * device and problem shape) a cached choice is reused without timing and new
  * choices are appended.  Allocates and frees temporary buffers; synchronises.
  * The chosen variants are returned in rows_minb / xfft_cols (may be NULL).

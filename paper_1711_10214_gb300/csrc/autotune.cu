@@ -31,7 +31,7 @@ std::string tune_key(const ashrt_plan* p, int batch) {
   char name[256] = "unknown";
   if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) snprintf(name, sizeof(name), "%s", prop.name);
   char buf[512];
-  snprintf(buf, sizeof(buf), "%s|variants=8|nt=%d|nx=%d|Nt=%d|Nx=%d|P=%d|shift=%d|B=%d", name,
+  snprintf(buf, sizeof(buf), "%s|variants=8b|nt=%d|nx=%d|Nt=%d|Nx=%d|P=%d|shift=%d|B=%d", name,
            p->nt, p->nx,
            p->Nt, p->Nx, p->P, p->shift ? 1 : 0, batch);
   return buf;
@@ -123,11 +123,17 @@ extern "C" ashrt_status ashrt_plan_autotune(ashrt_plan* p, int batch, const char
     return err;
   };
 
-  std::vector<int> minbs = {3};
-  if (p->logNt >= 9 && p->logNt <= 11) minbs = {3, 2, 1};
+  // the plan's default variant is timed first and kept unless another one is
+  // faster by more than 2% (timing noise does not flip the choice)
+  const int def_minb = p->rows_minb;
+  std::vector<int> minbs = {def_minb};
+  std::vector<int> cand = {3};
+  if (p->logNt >= 9 && p->logNt <= 11) cand = {3, 2, 1};
   if (rows16_supported(p->logNt) && p->tw_t16) {
-    for (int v : {4, 5, 6, 7, 8}) minbs.push_back(v);
+    for (int v : {4, 5, 6, 7, 8}) cand.push_back(v);
   }
+  for (int v : cand)
+    if (v != def_minb) minbs.push_back(v);
   std::vector<int> colss = {16};
   if (p->logNx <= 9) colss = {16, 8};
   double best = 1e30;
@@ -138,7 +144,7 @@ extern "C" ashrt_status ashrt_plan_autotune(ashrt_plan* p, int batch, const char
     double ms = 0.0;
     e = time_pair(&ms);
     if (e != cudaSuccess) break;
-    if (ms < best) {
+    if (ms < (mb == def_minb ? best : 0.98 * best)) {
       best = ms;
       best_minb = mb;
     }
@@ -148,7 +154,7 @@ extern "C" ashrt_status ashrt_plan_autotune(ashrt_plan* p, int batch, const char
     p->xfft_cols = colss[i];
     double ms = 0.0;
     e = time_pair(&ms);
-    if (e == cudaSuccess && ms < best) {
+    if (e == cudaSuccess && ms < 0.98 * best) {
       best = ms;
       best_cols = colss[i];
     }
