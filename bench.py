@@ -66,10 +66,10 @@ def _args():
                     help="gathers per call (the deblend workload is 64; smaller batches are "
                          "for profiling captures)")
     ap.add_argument("--variant", type=int, default=0,
-                    help="deblend mode: row-kernel variant 1..8 instead of the autotuner's "
+                    help="deblend mode: row-kernel variant 1..9 instead of the autotuner's "
                          "choice (profiling captures skip the autotuner's launches this way)")
     ap.add_argument("--rows-variant", type=int, default=0,
-                    help="ops mode: row-kernel variant 1..8 (0: the plan's default; see "
+                    help="ops mode: row-kernel variant 1..9 (0: the plan's default; see "
                          "ashrt_plan_set_variant)")
     return ap.parse_args()
 
@@ -136,7 +136,7 @@ def source_hash(kernel):
     return h.hexdigest()[:12]
 
 
-def measured_traffic(kernel, gathers, variant=(4, 16)):
+def measured_traffic(kernel, gathers, variant=(9, 16)):
     """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
     of `kernel` over `gathers` gathers, scaled from the committed ncu capture
     in profiles/dram_traffic.md (rows: | kernel | gathers per launch | bytes

@@ -336,7 +336,10 @@ ashrt_status ashrt_sort_gathers(const float* src_dev, int n0, int n1, int nt, fl
  * gather per CTA instead of an interleaved pair (half the shared memory, so
  * about twice the resident CTAs; per-bin tables read from L2 instead of
  * staged), 7: that forward with the radix-8 pair adjoint, 8: the radix-16
- * pair forward with that adjoint; the default is 4 where it applies, else 3)
+ * pair forward with that adjoint, 9: as 4 with the forward's per-bin sums in
+ * tensor memory instead of registers (Nt = 2048 only, four CTAs per SM
+ * instead of three; on other lengths the same kernels as 4); the default is 9
+ * at Nt = 2048, 4 at Nt = 1024 and 4096, else 3)
  * and the trace-axis FFT column tile (16 or 8 columns for Nx <= 512) -- and
  * keeps the fastest in the plan; the plan's current choice is timed first and
  * another one replaces it only when it is more than 2% faster, so variants
@@ -348,9 +351,9 @@ ashrt_status ashrt_sort_gathers(const float* src_dev, int n0, int n1, int nt, fl
  */
 ashrt_status ashrt_plan_autotune(ashrt_plan* plan, int batch, const char* cache_path,
                                  int* rows_minb, int* xfft_cols);
-/* Sets the variants directly (rows_minb 1..8, xfft_cols 8 or 16); register
+/* Sets the variants directly (rows_minb 1..9, xfft_cols 8 or 16); register
  * caps and column tiles that do not apply to the plan's sizes fall back to the
- * default kernel; rows_minb 4..8 on an Nt other than 1024, 2048 or 4096 is
+ * default kernel; rows_minb 4..9 on an Nt other than 1024, 2048 or 4096 is
  * ASHRT_EINVAL. */
 ashrt_status ashrt_plan_set_variant(ashrt_plan* plan, int rows_minb, int xfft_cols);
 

@@ -31,7 +31,7 @@ std::string tune_key(const ashrt_plan* p, int batch) {
   char name[256] = "unknown";
   if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) snprintf(name, sizeof(name), "%s", prop.name);
   char buf[512];
-  snprintf(buf, sizeof(buf), "%s|variants=8b|nt=%d|nx=%d|Nt=%d|Nx=%d|P=%d|shift=%d|B=%d", name,
+  snprintf(buf, sizeof(buf), "%s|variants=9|nt=%d|nx=%d|Nt=%d|Nx=%d|P=%d|shift=%d|B=%d", name,
            p->nt, p->nx,
            p->Nt, p->Nx, p->P, p->shift ? 1 : 0, batch);
   return buf;
@@ -131,6 +131,7 @@ extern "C" ashrt_status ashrt_plan_autotune(ashrt_plan* p, int batch, const char
   if (p->logNt >= 9 && p->logNt <= 11) cand = {3, 2, 1};
   if (rows16_supported(p->logNt) && p->tw_t16) {
     for (int v : {4, 5, 6, 7, 8}) cand.push_back(v);
+    if (p->logNt == 11) cand.push_back(9);
   }
   for (int v : cand)
     if (v != def_minb) minbs.push_back(v);
@@ -173,12 +174,12 @@ extern "C" ashrt_status ashrt_plan_autotune(ashrt_plan* p, int batch, const char
 }
 
 extern "C" ashrt_status ashrt_plan_set_variant(ashrt_plan* p, int rows_minb, int xfft_cols) {
-  if (!p || rows_minb < 1 || rows_minb > 8 || (xfft_cols != 8 && xfft_cols != 16)) {
-    set_error("ashrt_plan_set_variant: need a plan, rows_minb in 1..8, xfft_cols 8 or 16");
+  if (!p || rows_minb < 1 || rows_minb > 9 || (xfft_cols != 8 && xfft_cols != 16)) {
+    set_error("ashrt_plan_set_variant: need a plan, rows_minb in 1..9, xfft_cols 8 or 16");
     return ASHRT_EINVAL;
   }
   if (rows_minb >= 4 && !p->tw_t16) {
-    set_error("ashrt_plan_set_variant: the radix-16 row kernels (4..8) need Nt = 1024, 2048 or "
+    set_error("ashrt_plan_set_variant: the radix-16 row kernels (4..9) need Nt = 1024, 2048 or "
               "4096");
     return ASHRT_EINVAL;
   }

@@ -77,7 +77,8 @@ struct RowArgs {
                                    // adjoint; 5 radix-16 both; 6 single-gather radix-16
                                    // both; 7 single-gather radix-16 forward, radix-8
                                    // adjoint; 8 radix-16 pair forward, single-gather
-                                   // radix-16 adjoint (4..8 need tw16)
+                                   // radix-16 adjoint; 9 as 4 with the forward's
+                                   // accumulator in tensor memory (4..9 need tw16)
 };
 
 cudaError_t launch_xfft_r2c(const XfftArgs& a, cudaStream_t s);
@@ -87,6 +88,7 @@ cudaError_t launch_stolt_adj_rows(const RowArgs& a, cudaStream_t s);
 // Radix-16 row kernels (Nt = 1024, 2048, 4096 only; see stolt_r16.cu).
 bool rows16_supported(int logNt);
 cudaError_t launch_stolt_fwd_rows16(const RowArgs& a, cudaStream_t s);
+cudaError_t launch_stolt_fwd_rows16_tm(const RowArgs& a, cudaStream_t s);
 cudaError_t launch_stolt_adj_rows16(const RowArgs& a, cudaStream_t s);
 // Single-gather radix-16 row kernels (Nt = 1024, 2048, 4096; see stolt_r16s.cu).
 cudaError_t launch_stolt_fwd_rows16s(const RowArgs& a, cudaStream_t s);
@@ -181,7 +183,7 @@ struct ashrt_plan {
   int with_solver = 0;
   ashrt_opts opts{};
   bool shift = false;        // any nonzero tau0
-  int rows_minb = 3;         // row-kernel variant 1..8 (autotuned; see ashrt_plan_autotune)
+  int rows_minb = 3;         // row-kernel variant 1..9 (autotuned; see ashrt_plan_autotune)
   int xfft_cols = 16;
   // device tables
   float2* tw_t = nullptr;

@@ -77,10 +77,13 @@ stolt_adj_rows(RowArgs a) {
   float2* xA = a.Xw + (long long)b0 * a.x_batch + (long long)l * a.ld;
   float2* xB = hasB ? xA + a.x_batch : nullptr;
   int iv = 0, jt = 0;
+  int km = __ldg(a.kmin + l);                   // cone start of the panel's (velocity, k_x)
   for (int p = 0; p < a.P; ++p) {
     cp_async_wait_all();
     __syncthreads();
-    const bool mapped = __ldg(a.kmin + iv * a.Lh + l) < H;
+    const bool mapped = km < H;
+    // the next panel's, loaded a panel ahead of its use
+    if (p + 1 < a.P) km = __ldg(a.kmin + (iv + 1 == a.nv ? 0 : iv + 1) * a.Lh + l);
     const float2* phj = SHIFT ? a.phase + (long long)jt * N : nullptr;
     // the bins this thread gathers, j = tid + T s, are exactly the inputs of
     // its first inverse-FFT butterfly: they stay in registers

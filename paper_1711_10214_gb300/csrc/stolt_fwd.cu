@@ -169,10 +169,12 @@ cudaError_t launch_fwd_t(const RowArgs& a, cudaStream_t s) {
 }  // namespace
 
 // Variants (a.minb): 1..3 radix-8 with that register cap; 4, 5 and 8 use the
-// radix-16 pair forward (stolt_r16.cu), 6 and 7 the single-gather radix-16
+// radix-16 pair forward (stolt_r16.cu), 9 its tensor-memory-accumulator form
+// (Nt = 2048; the register form elsewhere), 6 and 7 the single-gather radix-16
 // forward (stolt_r16s.cu) where their twiddles exist, else cap 3.
 cudaError_t launch_stolt_fwd_rows(const RowArgs& a, cudaStream_t s) {
   if ((a.minb == 6 || a.minb == 7) && a.tw16) return launch_stolt_fwd_rows16s(a, s);
+  if (a.minb == 9 && a.tw16) return launch_stolt_fwd_rows16_tm(a, s);
   if (a.minb >= 4 && a.tw16) return launch_stolt_fwd_rows16(a, s);
   RowArgs b = a;
   if (b.minb > 3) b.minb = 3;

@@ -155,10 +155,13 @@ stolt_adj_rows16(RowArgs a) {
   float2* xA = a.Xw + (long long)b0 * a.x_batch + (long long)l * a.ld;
   float2* xB = hasB ? xA + a.x_batch : nullptr;
   int iv = 0, jt = 0;
+  int km = __ldg(a.kmin + l);                   // cone start of the panel's (velocity, k_x)
   for (int p = 0; p < a.P; ++p) {
     cp_async_wait_all();
     __syncthreads();
-    const bool mapped = __ldg(a.kmin + iv * a.Lh + l) < H;
+    const bool mapped = km < H;
+    // the next panel's, loaded a panel ahead of its use
+    if (p + 1 < a.P) km = __ldg(a.kmin + (iv + 1 == a.nv ? 0 : iv + 1) * a.Lh + l);
     const float2* phj = SHIFT ? a.phase + (long long)jt * N : nullptr;
     float4 accs[16];
 #pragma unroll
@@ -181,6 +184,199 @@ stolt_adj_rows16(RowArgs a) {
       ++jt;
     }
   }
+}
+
+// Tensor-memory accumulator of the forward rows: 16 bins x float4 = 64 words
+// per thread, in 64 TMEM columns of the thread's own lane (a warp reaches only
+// its quarter of the 128 lanes: warp w of a 128-thread CTA owns lanes
+// 32w..32w+31).  Loads complete at tcgen05.wait::ld, which takes the loaded
+// registers as operands so that no use is scheduled before it.
+__device__ __forceinline__ void tm_ld16(uint32_t ta, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+}
+__device__ __forceinline__ void tm_wait_ld(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tm_st16(uint32_t ta, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};\n" ::"r"(ta),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all_but_1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+constexpr int kTmCols = 64;   // TMEM columns per CTA (power of two >= 32)
+
+// Forward rows for Nt = 2048 with the accumulator in tensor memory: as
+// stolt_fwd_rows16<11>, but each thread's 16 accumulated bins live in TMEM
+// instead of 64 registers, and the tap row is single-buffered (staged at the
+// end of a panel, waited for before the next map), so that 128 registers and
+// 53 KB of shared memory per CTA let four CTAs share an SM instead of three:
+// the kernel is issue-bound and hides its shared-memory latency with the extra
+// warps.  Four CTAs hold 256 of an SM's 512 TMEM columns, so tcgen05.alloc
+// never waits.  cp.async groups, in commit order: rows of panel p, taps of
+// panel p, rows of p + 1, taps of p + 1, ... (a group may be empty), so
+// "all but the newest group complete" is the rows at the start of a panel and
+// the taps before its map.
+template <bool SHIFT, bool HALF>
+__global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
+  constexpr int LOGN = 11, N = 1 << LOGN, T = N / 16;
+  using S = Sched16<LOGN>;
+  extern __shared__ float4 smem4[];
+  float4* buf = smem4;                          // N interleaved (A, B) values
+  float2* stage = (float2*)(smem4 + N);         // next panel: row A [ld], row B [ld]
+  unsigned* stap = (unsigned*)(stage + 2 * a.ld);
+  uint32_t* tslot = (uint32_t*)(stap + a.taps_ld);
+  const int tid = threadIdx.x, warp = tid >> 5, l = blockIdx.x, b0 = 2 * blockIdx.y;
+  const bool hasB = b0 + 1 < a.batch;
+  const float2* xA = a.X + (long long)b0 * a.x_batch + (long long)l * a.ld;
+  const float2* xB = hasB ? xA + a.x_batch : nullptr;
+  const unsigned* trow = a.taps + (long long)l * a.taps_ld;
+  const long long tstep = (long long)a.Lh * a.taps_ld;
+  stage_rows(stage, xA, xB, a.ld, tid, T);
+  cp_async_commit();
+  stage_taps(stap, trow, a.taps_ld, tid, T);
+  cp_async_commit();
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(tslot)),
+                 "r"((uint32_t)kTmCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tacc = *tslot + ((uint32_t)(32 * warp) << 16);
+  {
+    uint32_t z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = 0u;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tm_st16(tacc + 16 * c, z);
+  }
+
+  int iv = 0, jt = 0;
+  for (int p = 0; p < a.P; ++p) {
+    cp_async_wait_all_but_1();                  // rows of panel p
+    __syncthreads();
+    float4 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = tid + r * T;
+      if (HALF && r >= 8) {
+        v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      const float2 za = i < a.nt ? stage[i] : make_float2(0.f, 0.f);
+      const float2 zb = (hasB && i < a.nt) ? stage[a.ld + i] : make_float2(0.f, 0.f);
+      v[r] = pack2(za, zb);
+    }
+    __syncthreads();
+    if (p + 1 < a.P) {
+      const long long o = (long long)(p + 1) * a.x_panel;
+      stage_rows(stage, xA + o, hasB ? xB + o : nullptr, a.ld, tid, T);
+    }
+    cp_async_commit();
+    r16_first_pass<-1, float4, HALF>(buf, v, tid);
+    r16_pass_range<-1, LOGN, 1, S::NPASS, float4, true>(buf, a.tw16, tid);   // natural, unswizzled
+    cp_async_wait_all_but_1();                  // taps of panel p
+    __syncthreads();
+    tm_wait_st();                               // the previous panel's sums are in TMEM
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint32_t r[16];
+      tm_ld16(tacc + 16 * c, r);
+      float4 vk[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int s = 4 * c + j, k = tid + T * s;
+        const bool pos = s < 8;                    // k < N/2 exactly for the first half of s
+        const Tap t = tap_decode_side<N>(k, stap[pos ? k : N - k], pos);
+        vk[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t.valid) {
+          vk[j] = cscale(buf[t.i0], t.w0);
+          vk[j] = cfma(t.w1, buf[t.i1], vk[j]);
+          if (SHIFT) vk[j] = cmul(vk[j], __ldg(a.phase + (long long)jt * N + k));
+        }
+      }
+      tm_wait_ld(r);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        r[4 * j] = __float_as_uint(__uint_as_float(r[4 * j]) + vk[j].x);
+        r[4 * j + 1] = __float_as_uint(__uint_as_float(r[4 * j + 1]) + vk[j].y);
+        r[4 * j + 2] = __float_as_uint(__uint_as_float(r[4 * j + 2]) + vk[j].z);
+        r[4 * j + 3] = __float_as_uint(__uint_as_float(r[4 * j + 3]) + vk[j].w);
+      }
+      tm_st16(tacc + 16 * c, r);
+    }
+    if (++iv == a.nv) {
+      iv = 0;
+      ++jt;
+    }
+    __syncthreads();                            // reads of buf and of the tap row done
+    if (p + 1 < a.P) {
+      const int ivn = iv;                         // the next panel's velocity index
+      stage_taps(stap, trow + ivn * tstep, a.taps_ld, tid, T);
+    }
+    cp_async_commit();
+  }
+  tm_wait_st();
+  float4 acc[16];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    uint32_t r[16];
+    tm_ld16(tacc + 16 * c, r);
+    tm_wait_ld(r);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      acc[4 * c + j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                   __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(*tslot),
+                 "r"((uint32_t)kTmCols));
+  }
+#pragma unroll
+  for (int s = 0; s < 16; ++s) acc[s] = cscale(acc[s], __ldg(a.wt + tid + T * s));
+  r16_first_pass<+1>(buf, acc, tid);
+  r16_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw16, tid);
+  float2* yA = a.Yw + (long long)b0 * a.y_batch + (long long)l * a.ld;
+  r16_last_pass_global<+1, LOGN>(buf, a.tw16, tid, yA, hasB ? yA + a.y_batch : nullptr, a.nt);
+}
+
+template <bool SHIFT, bool HALF>
+cudaError_t launch_fwd16_tm_h(const RowArgs& a, cudaStream_t s) {
+  constexpr int N = 1 << 11;
+  static bool attr = false;
+  const size_t smem = (size_t)N * sizeof(float4) + (size_t)2 * a.ld * sizeof(float2) +
+                      (size_t)a.taps_ld * sizeof(unsigned) + 16;
+  cudaError_t e = set_smem(stolt_fwd_rows16_tm<SHIFT, HALF>, smem_cap<11>(true), attr);
+  if (e != cudaSuccess) return e;
+  stolt_fwd_rows16_tm<SHIFT, HALF><<<dim3(a.Lh, (a.batch + 1) / 2), N / 16, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <int LOGN, bool SHIFT, bool HALF>
@@ -225,6 +421,15 @@ cudaError_t launch_stolt_fwd_rows16(const RowArgs& a, cudaStream_t s) {
     case 12: return sh ? launch_fwd16<12, true>(a, s) : launch_fwd16<12, false>(a, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// The tensor-memory forward (Nt = 2048 only; other lengths take the register form).
+cudaError_t launch_stolt_fwd_rows16_tm(const RowArgs& a, cudaStream_t s) {
+  if (!a.tw16) return cudaErrorInvalidValue;
+  if (row_log2(a.Nt) != 11) return launch_stolt_fwd_rows16(a, s);
+  const bool sh = a.phase != nullptr, half = 2 * a.nt <= a.Nt;
+  if (sh) return half ? launch_fwd16_tm_h<true, true>(a, s) : launch_fwd16_tm_h<true, false>(a, s);
+  return half ? launch_fwd16_tm_h<false, true>(a, s) : launch_fwd16_tm_h<false, false>(a, s);
 }
 
 cudaError_t launch_stolt_adj_rows16(const RowArgs& a, cudaStream_t s) {

@@ -181,13 +181,16 @@ stolt_adj_rows16s(RowArgs a) {
 
   float2* xr = a.Xw + (long long)b * a.x_batch + (long long)l * a.ld;
   int iv = 0, jt = 0;
+  int km = __ldg(a.kmin + l);                   // cone start of the panel's (velocity, k_x)
   for (int p = 0; p < a.P; ++p) {
     // dsp complete (first panel); the previous panel's reads of buf done
     __syncthreads();
     const long long o = (long long)p * a.x_panel;
     const int ivn = iv + 1 == a.nv ? 0 : iv + 1;
     const bool more = p + 1 < a.P;
-    if (__ldg(a.kmin + iv * a.Lh + l) >= H) {
+    const bool unmapped = km >= H;
+    if (more) km = __ldg(a.kmin + ivn * a.Lh + l);   // the next panel's, a panel ahead
+    if (unmapped) {
       // no bin of this (velocity, k_x) row is mapped: the panel row is zero
       for (int i = tid; i < a.nt; i += T) xr[o + i] = make_float2(0.f, 0.f);
       if (more) {

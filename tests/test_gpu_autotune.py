@@ -29,7 +29,7 @@ def test_every_variant_matches_oracle(lib):
     ref_m = stolt.adjoint_batch(g, d)
     dev = torch.device("cuda:0")
     md, dd = torch.from_numpy(m).to(dev), torch.from_numpy(d).to(dev)
-    for minb in (1, 2, 3, 4, 5, 6, 7, 8):
+    for minb in (1, 2, 3, 4, 5, 6, 7, 8, 9):
         for cols in (8, 16):
             plan.set_variant(minb, cols)
             od, om = torch.empty_like(dd), torch.empty_like(md)
@@ -46,7 +46,7 @@ def test_autotune_choice_and_cache(lib, tmp_path):
     plan = ashrt.Plan(300, 100, DT, DX, [1500.0, 2600.0], max_batch=4)
     cache = str(tmp_path / "tune.jsonl")
     mb, cols = plan.autotune(batch=4, cache_path=cache)
-    assert mb in range(1, 9) and cols in (8, 16)
+    assert mb in range(1, 10) and cols in (8, 16)
     lines = [json.loads(x) for x in open(cache)]
     assert len(lines) == 1 and lines[0]["rows_minb"] == mb and lines[0]["xfft_cols"] == cols
     plan2 = ashrt.Plan(300, 100, DT, DX, [1500.0, 2600.0], max_batch=4)
@@ -66,8 +66,10 @@ def test_autotune_choice_and_cache(lib, tmp_path):
 def test_radix16_rows_match_oracle(lib, nt, nx, v, t0, batch, mask, kw):
     """The radix-16 row kernels on every length they serve, in both CTA
     shapes (variant 5: an interleaved gather pair per CTA; variant 6: one
-    gather per CTA, tables read from L2), with the asymptote shift, the
-    sampling mask and an odd batch (a lone gather in the last pair)."""
+    gather per CTA, tables read from L2) and with the forward's accumulator in
+    tensor memory (variant 9, Nt 2048; the register form on other lengths),
+    with the asymptote shift, the sampling mask and an odd batch (a lone
+    gather in the last pair)."""
     import torch
     from paper_1711_10214_gb300 import ashrt
     plan = ashrt.Plan(nt, nx, DT, DX, v, t0s=t0, max_batch=batch, **kw)
@@ -80,7 +82,7 @@ def test_radix16_rows_match_oracle(lib, nt, nx, v, t0, batch, mask, kw):
     dev = torch.device("cuda:0")
     md, dd = torch.from_numpy(m).to(dev), torch.from_numpy(d).to(dev)
     mkd = torch.from_numpy(mk).to(dev) if mask else None
-    for variant in (5, 6):
+    for variant in (5, 6, 9):
         plan.set_variant(variant, 16)
         od, om = torch.full_like(dd, float("nan")), torch.full_like(md, float("nan"))
         plan.forward(md, od, mask=mkd, batch=batch)
@@ -91,17 +93,19 @@ def test_radix16_rows_match_oracle(lib, nt, nx, v, t0, batch, mask, kw):
     plan.close()
 
 
-def test_single_gather_rows_dot_test_and_dead_rows(lib):
-    """Variant 6 on the benchmark's row length (Nt 2048) with velocities fast
-    enough that whole (velocity, k_x) rows lie outside the cone (their panel
-    rows are written as zeros without a transform): parity with the oracle and
-    the FP32 dot test <L m, d> = <m, L^T d>."""
+@pytest.mark.parametrize("variant", [6, 9])
+def test_single_gather_rows_dot_test_and_dead_rows(lib, variant):
+    """Variants 6 (single-gather rows) and 9 (tensor-memory forward
+    accumulator) on the benchmark's row length (Nt 2048) with velocities fast
+    enough that whole (velocity, k_x) rows lie outside the cone (variant 6
+    writes their panel rows as zeros without a transform): parity with the
+    oracle and the FP32 dot test <L m, d> = <m, L^T d>."""
     import torch
     from paper_1711_10214_gb300 import ashrt
     nt, nx, v, B = 1000, 40, [1500.0, 6000.0, 9000.0], 3
     plan = ashrt.Plan(nt, nx, DT, DX, v, max_batch=B, wavelet_peak_hz=25.0)
     assert plan.Nt == 2048
-    plan.set_variant(6, 16)
+    plan.set_variant(variant, 16)
     g = stolt.Geometry(nt, nx, DT, DX, v, wavelet_peak_hz=25.0)
     a = g.cone_a(9000.0)
     assert np.sum(a[: g.Nx // 2 + 1] >= g.Nt // 2) > 0       # some rows fully outside
@@ -132,10 +136,13 @@ def test_radix16_rejected_where_it_does_not_apply(lib):
             plan.set_variant(variant, 16)
     with pytest.raises(ashrt.AshrtError):
         plan.set_variant(9, 16)
+    with pytest.raises(ashrt.AshrtError):
+        plan.set_variant(10, 16)
     plan.close()
 
 
-@pytest.mark.parametrize("nt,nx,variants", [(120, 20, (1, 2, 3)), (1000, 24, (4, 5, 6, 7, 8))])
+@pytest.mark.parametrize("nt,nx,variants", [(120, 20, (1, 2, 3)), (1000, 24, (4, 5, 6, 7, 8)),
+                                            (1500, 20, (4, 9))])
 def test_unpadded_time_axis_every_variant(lib, nt, nx, variants):
     """pad_t = 1: the model rows fill more than half of each time transform,
     so the forward kernels run their general first pass (with the default

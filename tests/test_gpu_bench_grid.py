@@ -43,7 +43,7 @@ def oracle_solve():
     return c, out
 
 
-@pytest.mark.parametrize("variant", [None, 4, 6])
+@pytest.mark.parametrize("variant", [None, 4, 6, 9])
 def test_deblend_parity_on_the_benchmark_grid(lib, oracle_solve, variant):
     import torch
     from paper_1711_10214_gb300 import ashrt
