@@ -336,9 +336,9 @@ ashrt_status ashrt_sort_gathers(const float* src_dev, int n0, int n1, int nt, fl
  * gather per CTA instead of an interleaved pair (half the shared memory, so
  * about twice the resident CTAs; per-bin tables read from L2 instead of
  * staged), 7: that forward with the radix-8 pair adjoint, 8: the radix-16
- * pair forward with that adjoint, 9: as 4 with the forward's per-bin sums in
+ * pair forward with that adjoint, 9: as 5 with the forward's per-bin sums in
  * tensor memory instead of registers (Nt = 2048 only, four CTAs per SM
- * instead of three; on other lengths the same kernels as 4); the default is 9
+ * instead of three; on other lengths the same kernels as 5); the default is 9
  * at Nt = 2048, 4 at Nt = 1024 and 4096, else 3)
  * and the trace-axis FFT column tile (16 or 8 columns for Nx <= 512) -- and
  * keeps the fastest in the plan; the plan's current choice is timed first and

@@ -215,6 +215,17 @@ __device__ __forceinline__ int swz_e(int i) {
   if constexpr (sizeof(E) == 16) return swz4(i);
   else return swz(i);
 }
+// The swizzle XORs bits [SB, SB + 3) (float4) or [SB, SB + 4) (float2) into the
+// low bits, SB the log2 of the elements per bank row.  Adding a multiple of
+// 2^(2 SB) (float4: 64, float2: 256) to an index whose bits at and above that
+// power are zero changes neither those bits nor the XOR term, so
+// swz(i + c) = swz(i) + c: a pass whose element strides are such multiples
+// swizzles one base index per butterfly and reaches the others at constant
+// offsets.
+template <typename E>
+__host__ __device__ constexpr bool swz_e_shift_free(int c) {
+  return c % (sizeof(E) == 16 ? 64 : 256) == 0;
+}
 
 // Base twiddle of pass q: exp(DIR 2 pi i k / (Ns R)) read from the per-length
 // table (stored for DIR = -1; conjugated for the synthesis direction).
@@ -237,14 +248,19 @@ __device__ __forceinline__ void row_pass(E* buf, int Ns, const float2* __restric
                                          int tw_off, int tid) {
   constexpr int T = N / 8;
   constexpr int NB = 8 / R;
+  constexpr bool rd_lin = swz_e_shift_free<E>(N / R);   // jb < N/R
   E v[8];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
+    const int jbs = swz_e<E>(jb);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz_e<E>(jb + r * (N / R))];
+    for (int r = 0; r < R; ++r)
+      v[q * R + r] = buf[rd_lin ? jbs + r * (N / R) : swz_e<E>(jb + r * (N / R))];
   }
   __syncthreads();
+  // base = (jb - k) R + k has zero bits from Ns up to Ns R, where r Ns lands
+  const bool wr_lin = swz_e_shift_free<E>(Ns);
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
@@ -252,10 +268,11 @@ __device__ __forceinline__ void row_pass(E* buf, int Ns, const float2* __restric
     if (Ns > 1) twiddle_r<R>(&v[q * R], base_twiddle<DIR>(tw, tw_off, k));
     dft_r<DIR, R>(&v[q * R]);
     const int base = (jb - k) * R + k;
+    const int bases = PLAIN_OUT ? base : swz_e<E>(base);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int o = base + r * Ns;
-      buf[PLAIN_OUT ? o : swz_e<E>(o)] = v[q * R + r];
+      buf[PLAIN_OUT ? o : (wr_lin ? bases + r * Ns : swz_e<E>(o))] = v[q * R + r];
     }
   }
   __syncthreads();
@@ -297,12 +314,15 @@ __device__ __forceinline__ void row_last_pass_global(E* buf, const float2* __res
   constexpr int Q = S::NPASS - 1;
   constexpr int R = S::radix(Q);
   constexpr int N = S::N, T = N / 8, NB = 8 / R, Ns = S::ns(Q);
+  constexpr bool rd_lin = swz_e_shift_free<E>(N / R);   // jb < N/R
   E v[8];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
+    const int jbs = swz_e<E>(jb);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz_e<E>(jb + r * (N / R))];
+    for (int r = 0; r < R; ++r)
+      v[q * R + r] = buf[rd_lin ? jbs + r * (N / R) : swz_e<E>(jb + r * (N / R))];
   }
   __syncthreads();
 #pragma unroll

@@ -77,7 +77,7 @@ struct RowArgs {
                                    // adjoint; 5 radix-16 both; 6 single-gather radix-16
                                    // both; 7 single-gather radix-16 forward, radix-8
                                    // adjoint; 8 radix-16 pair forward, single-gather
-                                   // radix-16 adjoint; 9 as 4 with the forward's
+                                   // radix-16 adjoint; 9 as 5 with the forward's
                                    // accumulator in tensor memory (4..9 need tw16)
 };
 

@@ -147,12 +147,12 @@ cudaError_t launch_adj_t(const RowArgs& a, cudaStream_t s) {
 }  // namespace
 
 // Variants (a.minb): 1..3 radix-8 with that register cap; 4 and 7 radix-8
-// cap 3 (the forward alone is radix-16); 5 the radix-16 pair adjoint
+// cap 3 (the forward alone is radix-16); 5 and 9 the radix-16 pair adjoint
 // (stolt_r16.cu), 6 and 8 the single-gather radix-16 adjoint (stolt_r16s.cu)
 // where their twiddles exist, else cap 3.
 cudaError_t launch_stolt_adj_rows(const RowArgs& a, cudaStream_t s) {
   if ((a.minb == 6 || a.minb == 8) && a.tw16) return launch_stolt_adj_rows16s(a, s);
-  if (a.minb == 5 && a.tw16) return launch_stolt_adj_rows16(a, s);
+  if ((a.minb == 5 || a.minb == 9) && a.tw16) return launch_stolt_adj_rows16(a, s);
   RowArgs b = a;
   if (b.minb > 3) b.minb = 3;
   switch (row_log2(b.Nt)) {

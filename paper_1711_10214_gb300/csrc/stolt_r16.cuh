@@ -165,6 +165,13 @@ __device__ __forceinline__ int swz16(int i) {
   if constexpr (sizeof(E) == 16) return i ^ ((i >> 4) & 7);
   else return i ^ ((i >> 4) & 15);
 }
+// swz16(i + c) = swz16(i) + c when c is a multiple of 128 (float4) or 256
+// (float2) and i has no bits at or above c's lowest set bit: the XOR term
+// reads bits 4..6 (4..7) only.
+template <typename E>
+__host__ __device__ constexpr bool swz16_shift_free(int c) {
+  return c % (sizeof(E) == 16 ? 128 : 256) == 0;
+}
 
 // One in-place Stockham pass, T = N/16 threads, each with 16 / R butterflies
 // of radix R; PLAIN_OUT as in row_pass (common.cuh).
@@ -172,14 +179,19 @@ template <int DIR, int N, int R, typename E, bool PLAIN_OUT = false>
 __device__ __forceinline__ void r16_pass(E* buf, int Ns, const float2* __restrict__ tw, int off,
                                          int tid) {
   constexpr int T = N / 16, NB = 16 / R;
+  constexpr bool rd_lin = swz16_shift_free<E>(N / R);   // jb < N/R
   E v[16];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
+    const int jbs = swz16<E>(jb);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz16<E>(jb + r * (N / R))];
+    for (int r = 0; r < R; ++r)
+      v[q * R + r] = buf[rd_lin ? jbs + r * (N / R) : swz16<E>(jb + r * (N / R))];
   }
   __syncthreads();
+  // base = (jb - k) R + k has zero bits from Ns up to Ns R, where r Ns lands
+  const bool wr_lin = swz16_shift_free<E>(Ns);
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
@@ -187,10 +199,11 @@ __device__ __forceinline__ void r16_pass(E* buf, int Ns, const float2* __restric
     if (Ns > 1) twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, off, k));
     dft16_r<DIR, R>(&v[q * R]);
     const int base = (jb - k) * R + k;
+    const int bases = PLAIN_OUT ? base : swz16<E>(base);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int o = base + r * Ns;
-      buf[PLAIN_OUT ? o : swz16<E>(o)] = v[q * R + r];
+      buf[PLAIN_OUT ? o : (wr_lin ? bases + r * Ns : swz16<E>(o))] = v[q * R + r];
     }
   }
   __syncthreads();
@@ -229,12 +242,15 @@ __device__ __forceinline__ void r16_last_pass_global(const E* buf, const float2*
   using S = Sched16<LOGN>;
   constexpr int Q = S::NPASS - 1, R = S::radix(Q), N = S::N, T = N / 16, NB = 16 / R;
   constexpr int Ns = S::ns(Q);
+  constexpr bool rd_lin = swz16_shift_free<E>(N / R);   // jb < N/R
   E v[16];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
+    const int jbs = swz16<E>(jb);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = buf[swz16<E>(jb + r * (N / R))];
+    for (int r = 0; r < R; ++r)
+      v[q * R + r] = buf[rd_lin ? jbs + r * (N / R) : swz16<E>(jb + r * (N / R))];
   }
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
