@@ -356,21 +356,22 @@ xfft_r2c_tma(XfftArgs a, const __grid_constant__ R2cMaps mp, int n_tt, long long
   if (tid == 0) bulk_wait_all();
 }
 
-// Hermitian extension of a stored half spectrum for two adjacent columns at
-// once: row l of the full length-N spectrum; rows 0 and N/2 keep their real
-// parts only (real signal).  Returns (A, B) of columns t and t+1 (t even).
+// Stored row `row` (<= N/2) of the half spectrum for the two adjacent columns
+// t and t+1 (t even): (A, B) = (re, im of column t, re, im of column t+1).
 // Rows are ld >= nt long with ld a multiple of 4, so the 16-byte load at an
-// even t < nt stays inside the row; column t+1 >= nt is zeroed afterwards.
-template <int N>
-__device__ __forceinline__ float4 herm_load2(const float2* __restrict__ base, int ld, int row, int t,
-                                             int nt) {
-  const bool ok = t < nt;
-  const int r = row <= N / 2 ? row : N - row;
-  float4 y = __ldg((const float4*)(base + (long long)r * ld + (ok ? t : 0)));
-  const float sy = (row == 0 || row == N / 2) ? 0.f : (row > N / 2 ? -1.f : 1.f);
-  const bool okb = t + 1 < nt;
-  return make_float4(ok ? y.x : 0.f, ok ? y.y * sy : 0.f, okb ? y.z : 0.f, okb ? y.w * sy : 0.f);
+// even t < nt stays inside the row; a column >= nt reads as zero.
+__device__ __forceinline__ float4 col_load2(const float2* __restrict__ base, int ld, int row, int t,
+                                            int nt) {
+  const bool ok = t < nt, okb = t + 1 < nt;
+  const float4 y = __ldg((const float4*)(base + (long long)row * ld + (ok ? t : 0)));
+  return make_float4(ok ? y.x : 0.f, ok ? y.y : 0.f, okb ? y.z : 0.f, okb ? y.w : 0.f);
 }
+// Z = A + i B of a stored row (zdir), of its mirror N - row, whose A and B
+// are the conjugates (zmir), and of rows 0 and N/2, whose imaginary parts a
+// real signal's spectrum does not have (zreal).
+__device__ __forceinline__ float2 zdir(float4 y) { return make_float2(y.x - y.w, y.y + y.z); }
+__device__ __forceinline__ float2 zmir(float4 y) { return make_float2(y.x + y.w, y.z - y.y); }
+__device__ __forceinline__ float2 zreal(float4 y) { return make_float2(y.x, y.z); }
 
 // PF: the tile of the elementwise weight ew that this CTA's outputs use
 // ([nx][2C] floats) is copied into shared memory with cp.async when the CTA
@@ -400,20 +401,46 @@ xfft_c2r_kernel(XfftArgs a) {
     cp_async_commit();
   }
 
-  // first pass: Z = A + i B, A and B the Hermitian-extended spectra of columns ta, ta + 1
+  // first pass (radix 8: butterfly jb takes rows jb + r N/8) on Z = A + i B,
+  // A and B the Hermitian-extended spectra of columns ta, ta + 1.  Row
+  // jb + r N/8 > N/2 mirrors row (N/8 - jb) + (7 - r) N/8, so the thread
+  // takes butterflies jb and N/8 - jb together and builds their 16 inputs
+  // from 8 stored rows (jb = 0 pairs with N/16 = JS, each its own mirror:
+  // 9 rows, the Nyquist row included).
   float2 v[2][8];
+  const int jb0 = j0, jb1 = j0 == 0 ? JS : N / 8 - j0;
+  {
+    float4 ya[4], yb[4];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int jb = j0 + JS * q;
+    for (int r = 0; r < 4; ++r) {
+      ya[r] = col_load2(in, a.ld, jb0 + r * (N / 8), ta, a.nt);
+      yb[r] = col_load2(in, a.ld, jb1 + r * (N / 8), ta, a.nt);
+    }
+    if (j0 == 0) {
+      const float4 yn = col_load2(in, a.ld, N / 2, ta, a.nt);
+      v[0][0] = zreal(ya[0]);
+      v[0][4] = zreal(yn);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const float4 y = herm_load2<N>(in, a.ld, jb + r * (N / 8), ta, a.nt);
-      v[q][r] = make_float2(y.x - y.w, y.y + y.z);
+      for (int r = 1; r < 4; ++r) {
+        v[0][r] = zdir(ya[r]);
+        v[0][8 - r] = zmir(ya[r]);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        v[0][r] = zdir(ya[r]);
+        v[0][7 - r] = zmir(yb[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      v[1][r] = zdir(yb[r]);
+      v[1][7 - r] = j0 == 0 ? zmir(yb[r]) : zmir(ya[r]);
     }
   }
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const int jb = j0 + JS * q;
+    const int jb = q == 0 ? jb0 : jb1;
     dft8<+1>(v[q]);
 #pragma unroll
     for (int r = 0; r < 8; ++r) sm[(jb * 8 + r) * C + col] = v[q][r];
