@@ -378,8 +378,9 @@ __device__ __forceinline__ float2 zreal(float4 y) { return make_float2(y.x, y.z)
 // starts, so the epilogue reads it from there instead of waiting on global
 // loads after the transform (host condition: nt a multiple of 4, the tile
 // fits; 16-byte chunks wholly inside the row are copied, the rest are never
-// read).
-template <int LOGN, int C, bool PF>
+// read).  NXH: nx <= N/2, so outputs r >= R/2 of every last-pass butterfly
+// (traces jb + r N/R >= N/2) are cropped away and are not formed.
+template <int LOGN, int C, bool PF, bool NXH>
 __global__ void __launch_bounds__((1 << LOGN) * C / 16)
 xfft_c2r_kernel(XfftArgs a) {
   constexpr int N = 1 << LOGN, T = N * C / 16, JS = T / C;
@@ -473,7 +474,7 @@ xfft_c2r_kernel(XfftArgs a) {
     if (Ns > 1) twiddle_r<R>(&w[q * R], base_twiddle<+1>(a.tw, S::tw_off(Q), jb));
     dft_r<+1, R>(&w[q * R]);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < (NXH ? R / 2 : R); ++r) {
       const int row = jb + r * Ns;
       if (row < a.nx && ta < a.nt) {
         const long long o = (long long)row * a.nt + ta;
@@ -562,19 +563,25 @@ cudaError_t launch_r2c_tma(const XfftArgs& a, cudaStream_t s, bool* used) {
   return cudaGetLastError();
 }
 
-template <int LOGN, int C, bool PF>
-cudaError_t launch_c2r_pf(const XfftArgs& a, cudaStream_t s, size_t smem) {
+template <int LOGN, int C, bool PF, bool NXH>
+cudaError_t launch_c2r_k(const XfftArgs& a, cudaStream_t s, size_t smem) {
   constexpr int N = 1 << LOGN, T = N * C / 16;
   static size_t attr = 0;
   if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(xfft_c2r_kernel<LOGN, C, PF>,
+    cudaError_t e = cudaFuncSetAttribute(xfft_c2r_kernel<LOGN, C, PF, NXH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = smem;
   }
   dim3 grid(a.slabs, (a.nt + 2 * C - 1) / (2 * C));
-  xfft_c2r_kernel<LOGN, C, PF><<<grid, T, smem, s>>>(a);
+  xfft_c2r_kernel<LOGN, C, PF, NXH><<<grid, T, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int LOGN, int C, bool PF>
+cudaError_t launch_c2r_pf(const XfftArgs& a, cudaStream_t s, size_t smem) {
+  return 2 * a.nx <= (1 << LOGN) ? launch_c2r_k<LOGN, C, PF, true>(a, s, smem)
+                                 : launch_c2r_k<LOGN, C, PF, false>(a, s, smem);
 }
 
 // The weight tile goes through shared memory when there is a weight, its

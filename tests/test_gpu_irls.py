@@ -159,3 +159,24 @@ def test_warm_start_parity(lib, use_m0, use_wr0):
         assert _rel(drec[b], stolt.forward(g, m)) <= SEP_TOL, b
         np.testing.assert_allclose(reps[b]["misfit"], rep["misfit"], rtol=1e-3)
     plan.close()
+
+
+def test_unpadded_grid_deblend_parity(lib):
+    """pad_t = pad_x = 1 (nt 92 -> Nt 128, nx 21 -> Nx 32): the model and the
+    data fill more than half of each transform, so the kernels run their
+    general forms (the row kernels' full first pass, the trace-axis c2r with
+    its weight tile forming every output of its last pass, the TMA-fed r2c
+    with its fused CG update reading every row; nt is a multiple of 4 so that
+    both staged forms apply); the solve against the oracle IRLS."""
+    import torch
+    from paper_1711_10214_gb300 import ashrt
+    nt, nx, v, B = 92, 21, [1500.0, 2400.0], 2
+    plan = ashrt.Plan(nt, nx, DT, DX, v, max_batch=B, with_solver=True, pad_t=1, pad_x=1)
+    g = stolt.Geometry(nt, nx, DT, DX, v, pad_t=1, pad_x=1)
+    assert (plan.Nt, plan.Nx) == (g.Nt, g.Nx) == (128, 32)
+    rng = np.random.default_rng(12)
+    d = rng.standard_normal((B, nx, nt))
+    _, drec, _ = _run(torch, plan, d, p=1.0, q=1.0, n_outer=3, n_cg=6)
+    for b in range(B):
+        _, drec_o, _ = _oracle(g, d[b], p=1.0, q=1.0, n_outer=3, n_cg=6)
+        assert _rel(drec[b], drec_o) <= SEP_TOL, (b, _rel(drec[b], drec_o))
