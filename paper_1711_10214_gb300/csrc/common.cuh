@@ -306,7 +306,8 @@ __device__ __forceinline__ void store_out(float2* outA, float2* outB, int idx, f
   if (outB) outB[idx] = hi2(v);
 }
 
-template <int DIR, int LOGN, typename E>
+// KEEP_LOW: n_keep <= N/2, so outputs r >= R/2 (elements >= N/2) are not formed.
+template <int DIR, int LOGN, typename E, bool KEEP_LOW = false>
 __device__ __forceinline__ void row_last_pass_global(E* buf, const float2* __restrict__ tw,
                                                      int tid, float2* __restrict__ outA,
                                                      float2* __restrict__ outB, int n_keep) {
@@ -331,7 +332,7 @@ __device__ __forceinline__ void row_last_pass_global(E* buf, const float2* __res
     if (Ns > 1) twiddle_r<R>(&v[q * R], base_twiddle<DIR>(tw, S::tw_off(Q), jb));
     dft_r<DIR, R>(&v[q * R]);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < (KEEP_LOW ? R / 2 : R); ++r) {
       const int idx = jb + r * Ns;
       if (idx < n_keep) store_out(outA, outB, idx, v[q * R + r]);
     }

@@ -47,7 +47,7 @@ namespace {
 // directly.  Every output bin is written once, by its owner: no atomics, no
 // clearing pass, no search, and the strided ownership spreads the bins
 // outside the cone over all warps.
-template <int LOGN, bool SHIFT, int MINB>
+template <int LOGN, bool SHIFT, int MINB, bool HALF>
 __global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
 stolt_adj_rows(RowArgs a) {
   constexpr int N = 1 << LOGN, T = N / 8, H = N / 2;
@@ -103,7 +103,8 @@ stolt_adj_rows(RowArgs a) {
     }
     row_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw, tid);
     const long long o = (long long)p * a.x_panel;
-    row_last_pass_global<+1, LOGN>(buf, a.tw, tid, xA + o, hasB ? xB + o : nullptr, a.nt);
+    row_last_pass_global<+1, LOGN, float4, HALF>(buf, a.tw, tid, xA + o, hasB ? xB + o : nullptr,
+                                                 a.nt);
     if (++iv == a.nv) {
       iv = 0;
       ++jt;
@@ -112,15 +113,23 @@ stolt_adj_rows(RowArgs a) {
 }
 
 
-template <int LOGN, bool SHIFT, int MINB>
-cudaError_t launch_adj_v(const RowArgs& a, cudaStream_t s) {
+template <int LOGN, bool SHIFT, int MINB, bool HALF>
+cudaError_t launch_adj_vh(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
   const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.atab_ld * sizeof(uint2);
-  cudaError_t e = set_smem(stolt_adj_rows<LOGN, SHIFT, MINB>, smem_cap<LOGN>(false), attr);
+  cudaError_t e = set_smem(stolt_adj_rows<LOGN, SHIFT, MINB, HALF>, smem_cap<LOGN>(false), attr);
   if (e != cudaSuccess) return e;
-  stolt_adj_rows<LOGN, SHIFT, MINB><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
+  stolt_adj_rows<LOGN, SHIFT, MINB, HALF><<<dim3(a.Lh, (a.batch + 1) / 2), N / 8, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// HALF: nt <= Nt / 2, so each panel's inverse transform keeps only its
+// lower half and the last pass forms only those outputs.
+template <int LOGN, bool SHIFT, int MINB>
+cudaError_t launch_adj_v(const RowArgs& a, cudaStream_t s) {
+  return 2 * a.nt <= a.Nt ? launch_adj_vh<LOGN, SHIFT, MINB, true>(a, s)
+                          : launch_adj_vh<LOGN, SHIFT, MINB, false>(a, s);
 }
 
 // Register-cap variant: resident CTAs per SM the kernel is compiled for

@@ -123,7 +123,8 @@ stolt_fwd_rows(RowArgs a) {
   row_first_pass<+1, N>(buf, acc, tid);
   row_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw, tid);
   float2* yA = a.Yw + (long long)b0 * a.y_batch + (long long)l * a.ld;
-  row_last_pass_global<+1, LOGN>(buf, a.tw, tid, yA, hasB ? yA + a.y_batch : nullptr, a.nt);
+  row_last_pass_global<+1, LOGN, float4, HALF>(buf, a.tw, tid, yA,
+                                               hasB ? yA + a.y_batch : nullptr, a.nt);
 }
 
 

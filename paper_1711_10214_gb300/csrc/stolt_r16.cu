@@ -111,12 +111,13 @@ stolt_fwd_rows16(RowArgs a) {
   r16_first_pass<+1>(buf, acc, tid);
   r16_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw16, tid);
   float2* yA = a.Yw + (long long)b0 * a.y_batch + (long long)l * a.ld;
-  r16_last_pass_global<+1, LOGN>(buf, a.tw16, tid, yA, hasB ? yA + a.y_batch : nullptr, a.nt);
+  r16_last_pass_global<+1, LOGN, float4, HALF>(buf, a.tw16, tid, yA,
+                                               hasB ? yA + a.y_batch : nullptr, a.nt);
 }
 
 // Adjoint rows: as stolt_adj_rows (gather form of the transposed map over the
 // source table), with 16 output bins per thread.
-template <int LOGN, bool SHIFT>
+template <int LOGN, bool SHIFT, bool HALF>
 __global__ void __launch_bounds__((1 << LOGN) / 16, r16_minb<LOGN>())
 stolt_adj_rows16(RowArgs a) {
   constexpr int N = 1 << LOGN, T = N / 16, H = N / 2;
@@ -178,7 +179,8 @@ stolt_adj_rows16(RowArgs a) {
     }
     r16_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw16, tid);
     const long long o = (long long)p * a.x_panel;
-    r16_last_pass_global<+1, LOGN>(buf, a.tw16, tid, xA + o, xB ? xB + o : nullptr, a.nt);
+    r16_last_pass_global<+1, LOGN, float4, HALF>(buf, a.tw16, tid, xA + o, xB ? xB + o : nullptr,
+                                                 a.nt);
     if (++iv == a.nv) {
       iv = 0;
       ++jt;
@@ -364,7 +366,8 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
   r16_first_pass<+1>(buf, acc, tid);
   r16_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw16, tid);
   float2* yA = a.Yw + (long long)b0 * a.y_batch + (long long)l * a.ld;
-  r16_last_pass_global<+1, LOGN>(buf, a.tw16, tid, yA, hasB ? yA + a.y_batch : nullptr, a.nt);
+  r16_last_pass_global<+1, LOGN, float4, HALF>(buf, a.tw16, tid, yA,
+                                               hasB ? yA + a.y_batch : nullptr, a.nt);
 }
 
 template <bool SHIFT, bool HALF>
@@ -397,15 +400,23 @@ cudaError_t launch_fwd16(const RowArgs& a, cudaStream_t s) {
                           : launch_fwd16_h<LOGN, SHIFT, false>(a, s);
 }
 
-template <int LOGN, bool SHIFT>
-cudaError_t launch_adj16(const RowArgs& a, cudaStream_t s) {
+template <int LOGN, bool SHIFT, bool HALF>
+cudaError_t launch_adj16_h(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
   const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.atab_ld * sizeof(uint2);
-  cudaError_t e = set_smem(stolt_adj_rows16<LOGN, SHIFT>, smem_cap<LOGN>(false), attr);
+  cudaError_t e = set_smem(stolt_adj_rows16<LOGN, SHIFT, HALF>, smem_cap<LOGN>(false), attr);
   if (e != cudaSuccess) return e;
-  stolt_adj_rows16<LOGN, SHIFT><<<dim3(a.Lh, (a.batch + 1) / 2), N / 16, smem, s>>>(a);
+  stolt_adj_rows16<LOGN, SHIFT, HALF><<<dim3(a.Lh, (a.batch + 1) / 2), N / 16, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// HALF: nt <= Nt / 2, so each panel's inverse transform keeps only its
+// lower half and the last pass forms only those outputs.
+template <int LOGN, bool SHIFT>
+cudaError_t launch_adj16(const RowArgs& a, cudaStream_t s) {
+  return 2 * a.nt <= a.Nt ? launch_adj16_h<LOGN, SHIFT, true>(a, s)
+                          : launch_adj16_h<LOGN, SHIFT, false>(a, s);
 }
 
 }  // namespace

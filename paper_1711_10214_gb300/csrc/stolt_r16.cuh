@@ -234,8 +234,9 @@ __device__ __forceinline__ void r16_first_pass(E* buf, E* v, int tid) {
 
 // Last pass read from shared memory and stored to the global rows outA / outB
 // (outB may be null; unused for float2), keeping outputs with index < n_keep.
-// Ns = N/R > jb, so output r of butterfly jb is element jb + r Ns.
-template <int DIR, int LOGN, typename E>
+// Ns = N/R > jb, so output r of butterfly jb is element jb + r Ns.  KEEP_LOW:
+// n_keep <= N/2, so outputs r >= R/2 (elements >= N/2) are not formed.
+template <int DIR, int LOGN, typename E, bool KEEP_LOW = false>
 __device__ __forceinline__ void r16_last_pass_global(const E* buf, const float2* __restrict__ tw,
                                                      int tid, float2* __restrict__ outA,
                                                      float2* __restrict__ outB, int n_keep) {
@@ -258,7 +259,7 @@ __device__ __forceinline__ void r16_last_pass_global(const E* buf, const float2*
     twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, S::tw_off(Q), jb));
     dft16_r<DIR, R>(&v[q * R]);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < (KEEP_LOW ? R / 2 : R); ++r) {
       const int idx = jb + r * Ns;
       if (idx < n_keep) store_out(outA, outB, idx, v[q * R + r]);
     }
