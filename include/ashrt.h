@@ -408,9 +408,12 @@ ashrt_status ashrt_batch_deblend(ashrt_batch* batch, const float* d_dev, float* 
  *   ashrt_profile_read: synchronises on the recorded events and returns, per
  *     kernel class, the summed elapsed milliseconds and the number of timed
  *     launches since the previous read, then resets them.  Classes:
- *     0 trace-axis r2c FFT, 1 forward row kernel (t-FFT + Stolt map + sum),
- *     2 adjoint row kernel, 3 trace-axis c2r FFT, 4 solver vector kernels
- *     (counted only).  n is the length of ms / launches (up to 5).
+ *     0 model-side trace-axis r2c FFT (the forward's), 1 forward row kernel
+ *     (t-FFT + Stolt map + sum), 2 adjoint row kernel, 3 model-side
+ *     trace-axis c2r FFT (the adjoint's), 4 solver vector kernels (counted
+ *     only), 5 data-side trace-axis r2c (the adjoint's), 6 data-side
+ *     trace-axis c2r (the forward's).  n is the length of ms / launches (up
+ *     to 7).
  *     Returns 0, or 1 if an event could not be read.
  *   ashrt_kernel_launches: total kernels this library has launched in the
  *     process (all classes, profiling on or off).

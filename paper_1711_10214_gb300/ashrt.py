@@ -204,7 +204,8 @@ def _farr(x):
     return a, a.ctypes.data_as(ctypes.POINTER(c_float))
 
 
-PROFILE_CLASSES = ("xfft_r2c", "stolt_fwd_rows", "stolt_adj_rows", "xfft_c2r", "solver")
+PROFILE_CLASSES = ("xfft_r2c", "stolt_fwd_rows", "stolt_adj_rows", "xfft_c2r", "solver",
+                   "xfft_r2c_data", "xfft_c2r_data")
 
 
 def profile_enable(on=True):
@@ -213,9 +214,10 @@ def profile_enable(on=True):
 
 def profile_read():
     """{class: (total_ms, launches)} since the previous read (see ashrt_profile_read)."""
-    ms = (c_double * 5)()
-    cnt = (ctypes.c_longlong * 5)()
-    st = load().ashrt_profile_read(ms, cnt, 5)
+    n = len(PROFILE_CLASSES)
+    ms = (c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    st = load().ashrt_profile_read(ms, cnt, n)
     if st != 0:
         raise AshrtError(7, "profile events could not be read")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(PROFILE_CLASSES)}

@@ -141,8 +141,10 @@ void build_twiddle_table(int logn, float2* out, int lr = 3);
 void set_error(const char* fmt, ...);
 
 // Launch accounting / optional event timing per kernel class (prof.cu).
+// PROF_XR2C / PROF_XC2R: the model-side trace-axis transforms (forward r2c,
+// adjoint c2r); the data-side ones (one row per gather) have their own classes.
 enum ProfClass { PROF_XR2C = 0, PROF_ROWS_FWD = 1, PROF_ROWS_ADJ = 2, PROF_XC2R = 3,
-                 PROF_SOLVER = 4, kProfClasses = 5 };
+                 PROF_SOLVER = 4, PROF_XR2C_DATA = 5, PROF_XC2R_DATA = 6, kProfClasses = 7 };
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s);
 void count_launches(int n);

@@ -235,7 +235,7 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
   prof_end(PROF_ROWS_FWD, s);
   if (e != cudaSuccess) return e;
 
-  prof_begin(PROF_XC2R, s);
+  prof_begin(PROF_XC2R_DATA, s);
   if (p->irregular) {
     e = launch_irr_synth(p->Es, p->Y, d, p->nr, p->nt, p->Lh, p->ld, ra.y_batch, ew_data, tmask,
                          dot, batch, s);
@@ -250,7 +250,7 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
     ay.dot = dot;
     e = launch_xfft_c2r(ay, s);
   }
-  prof_end(PROF_XC2R, s);
+  prof_end(PROF_XC2R_DATA, s);
   return e;
 }
 
@@ -283,10 +283,10 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
       count_launches(1);
       if (e != cudaSuccess) return e;
     }
-    prof_begin(PROF_XR2C, s);
+    prof_begin(PROF_XR2C_DATA, s);
     e = launch_irr_analysis(p->Ea, d, p->Y, p->nr, p->nt, p->Lh, p->ld,
                             (long long)p->Lh * p->ld, ew_data, tmask, batch, s);
-    prof_end(PROF_XR2C, s);
+    prof_end(PROF_XR2C_DATA, s);
   } else {
     if (cg && cg->mode == 2) {
       ay.cg_mode = 2;
@@ -294,9 +294,9 @@ cudaError_t op_adjoint(const ashrt_plan* p, const float* d, float* m, const floa
       ay.cg_s = cg->s;
       ay.cg_coef = cg->coef;
     }
-    prof_begin(PROF_XR2C, s);
+    prof_begin(PROF_XR2C_DATA, s);
     e = launch_xfft_r2c(ay, s);
-    prof_end(PROF_XR2C, s);
+    prof_end(PROF_XR2C_DATA, s);
   }
   if (e != cudaSuccess) return e;
 
