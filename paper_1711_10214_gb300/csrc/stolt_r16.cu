@@ -25,6 +25,72 @@ namespace ashrt {
 
 namespace {
 
+// Tensor-memory words of a thread (the forward's accumulated bins, the
+// adjoint's twiddle powers) live in TMEM columns of the thread's own lane (a
+// warp reaches only its quarter of the 128 lanes: warp w of a 128-thread CTA
+// owns lanes 32w..32w+31).  Loads complete at tcgen05.wait::ld, which takes the loaded
+// registers as operands so that no use is scheduled before it.
+__device__ __forceinline__ void tm_ld16(uint32_t ta, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+}
+__device__ __forceinline__ void tm_wait_ld(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tm_st16(uint32_t ta, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};\n" ::"r"(ta),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all_but_1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+constexpr int kTmCols = 64;   // TMEM columns per CTA (power of two >= 32)
+
+// 16 float2 values through 32 TMEM columns of the thread's lane.
+__device__ __forceinline__ void tm_st_f2x16(uint32_t ta, const float2* v) {
+  uint32_t r[16];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      r[2 * i] = __float_as_uint(v[8 * h + i].x);
+      r[2 * i + 1] = __float_as_uint(v[8 * h + i].y);
+    }
+    tm_st16(ta + 16 * h, r);
+  }
+}
+__device__ __forceinline__ void tm_ld_f2x16(uint32_t ta, float2* v) {
+  uint32_t r0[16], r1[16];
+  tm_ld16(ta, r0);
+  tm_ld16(ta + 16, r1);
+  tm_wait_ld(r0);
+  tm_wait_ld(r1);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    v[i] = make_float2(__uint_as_float(r0[2 * i]), __uint_as_float(r0[2 * i + 1]));
+    v[8 + i] = make_float2(__uint_as_float(r1[2 * i]), __uint_as_float(r1[2 * i + 1]));
+  }
+}
+
 // Resident CTAs per SM each length is compiled for (register cap 65536 /
 // (threads x CTAs)): Nt 1024 -> 64 threads x 6, 2048 -> 128 x 3, 4096 -> 256 x 1
 // (the last is bound by shared memory to one CTA anyway).
@@ -126,6 +192,7 @@ stolt_adj_rows16(RowArgs a) {
   float4* buf = smem4;                          // per-panel w_tau spectrum, then its inverse FFT
   float4* dsp = smem4 + N;                      // data spectrum x W (both gathers)
   uint2* stab = (uint2*)(smem4 + 2 * N);        // source-table row of the current panel
+  uint32_t* tslot = (uint32_t*)(stab + a.atab_ld);
   const int tid = threadIdx.x, l = blockIdx.x, b0 = 2 * blockIdx.y;
   const bool hasB = b0 + 1 < a.batch;
   const float2* yA = a.Y + (long long)b0 * a.y_batch + (long long)l * a.ld;
@@ -134,6 +201,36 @@ stolt_adj_rows16(RowArgs a) {
   const long long astep = (long long)a.Lh * a.atab_ld;
   stage_tab(stab, arow, a.atab_ld, tid, T);
   cp_async_commit();
+
+  // Nt = 2048 (128 threads, one per TMEM lane): the inverse transform's
+  // twiddle powers depend on the thread and the pass, not on the panel.  They
+  // are formed once (by the products the passes would form) and kept in 64
+  // TMEM columns of the thread's lane: columns 0..31 the radix-16 pass's
+  // w^1..w^15, 32..63 the last pass's w^1..w^7 of its two butterflies.
+  constexpr bool TMT = LOGN == 11;
+  uint32_t tpw = 0;
+  if constexpr (TMT) {
+    const int warp = tid >> 5;
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                       (unsigned)__cvta_generic_to_shared(tslot)),
+                   "r"((uint32_t)kTmCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    tpw = *tslot + ((uint32_t)(32 * warp) << 16);
+    float2 pw[16];
+    pw[0] = make_float2(0.f, 0.f);
+    twiddle_powers<16>(base_twiddle<+1>(a.tw16, S::tw_off(1), tid & 15), pw);
+    tm_st_f2x16(tpw, pw);
+    pw[8] = make_float2(0.f, 0.f);
+    twiddle_powers<8>(base_twiddle<+1>(a.tw16, S::tw_off(2), tid), pw);
+    twiddle_powers<8>(base_twiddle<+1>(a.tw16, S::tw_off(2), tid + T), pw + 8);
+    tm_st_f2x16(tpw + 32, pw);
+    tm_wait_st();
+  }
 
   {
     float4 v[16];
@@ -177,56 +274,36 @@ stolt_adj_rows16(RowArgs a) {
       stage_tab(stab, arow + ivn * astep, a.atab_ld, tid, T);
       cp_async_commit();
     }
-    r16_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw16, tid);
     const long long o = (long long)p * a.x_panel;
-    r16_last_pass_global<+1, LOGN, float4, HALF>(buf, a.tw16, tid, xA + o, xB ? xB + o : nullptr,
-                                                 a.nt);
+    if constexpr (TMT) {
+      static_assert(S::NPASS == 3 && S::radix(1) == 16 && S::radix(2) == 8, "Nt 2048 schedule");
+      float2 pw[16];
+      tm_ld_f2x16(tpw, pw);
+      r16_pass<+1, N, 16, float4, false, true>(buf, S::ns(1), a.tw16, S::tw_off(1), tid, pw);
+      tm_ld_f2x16(tpw + 32, pw);
+      r16_last_pass_global<+1, LOGN, float4, HALF, true>(buf, a.tw16, tid, xA + o,
+                                                         xB ? xB + o : nullptr, a.nt, pw);
+    } else {
+      r16_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw16, tid);
+      r16_last_pass_global<+1, LOGN, float4, HALF>(buf, a.tw16, tid, xA + o,
+                                                   xB ? xB + o : nullptr, a.nt);
+    }
     if (++iv == a.nv) {
       iv = 0;
       ++jt;
     }
   }
+  if constexpr (TMT) {
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if ((tid >> 5) == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(*tslot),
+                   "r"((uint32_t)kTmCols));
+    }
+  }
 }
 
-// Tensor-memory accumulator of the forward rows: 16 bins x float4 = 64 words
-// per thread, in 64 TMEM columns of the thread's own lane (a warp reaches only
-// its quarter of the 128 lanes: warp w of a 128-thread CTA owns lanes
-// 32w..32w+31).  Loads complete at tcgen05.wait::ld, which takes the loaded
-// registers as operands so that no use is scheduled before it.
-__device__ __forceinline__ void tm_ld16(uint32_t ta, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(ta));
-}
-__device__ __forceinline__ void tm_wait_ld(uint32_t (&r)[16]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
-               :
-               : "memory");
-}
-__device__ __forceinline__ void tm_st16(uint32_t ta, const uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16};\n" ::"r"(ta),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
-      "r"(r[15])
-      : "memory");
-}
-__device__ __forceinline__ void tm_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all_but_1() {
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-}
-
-constexpr int kTmCols = 64;   // TMEM columns per CTA (power of two >= 32)
 
 // Forward rows for Nt = 2048 with the accumulator in tensor memory: as
 // stolt_fwd_rows16<11>, but each thread's 16 accumulated bins live in TMEM
@@ -234,8 +311,10 @@ constexpr int kTmCols = 64;   // TMEM columns per CTA (power of two >= 32)
 // end of a panel, waited for before the next map), so that 128 registers and
 // 53 KB of shared memory per CTA let four CTAs share an SM instead of three:
 // the kernel is issue-bound and hides its shared-memory latency with the extra
-// warps.  Four CTAs hold 256 of an SM's 512 TMEM columns, so tcgen05.alloc
-// never waits.  cp.async groups, in commit order: rows of panel p, taps of
+// warps.  TMEM per CTA: 128 columns, the sums in 0..63 and the twiddle powers
+// of the thread's butterflies (they depend on the thread and the pass, not on
+// the panel: formed once, by the products the passes would form) in 64..127;
+// four CTAs, the most that fit an SM, hold its 512 columns.  cp.async groups, in commit order: rows of panel p, taps of
 // panel p, rows of p + 1, taps of p + 1, ... (a group may be empty), so
 // "all but the newest group complete" is the rows at the start of a panel and
 // the taps before its map.
@@ -262,19 +341,29 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      (unsigned)__cvta_generic_to_shared(tslot)),
-                 "r"((uint32_t)kTmCols));
+                 "r"((uint32_t)(2 * kTmCols)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tacc = *tslot + ((uint32_t)(32 * warp) << 16);
+  const uint32_t tpw = tacc + kTmCols;
   {
     uint32_t z[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) z[i] = 0u;
 #pragma unroll
     for (int c = 0; c < 4; ++c) tm_st16(tacc + 16 * c, z);
+    static_assert(S::NPASS == 3 && S::radix(1) == 16 && S::radix(2) == 8, "Nt 2048 schedule");
+    float2 pw[16];
+    pw[0] = make_float2(0.f, 0.f);
+    twiddle_powers<16>(base_twiddle<-1>(a.tw16, S::tw_off(1), tid & 15), pw);
+    tm_st_f2x16(tpw, pw);
+    pw[8] = make_float2(0.f, 0.f);
+    twiddle_powers<8>(base_twiddle<-1>(a.tw16, S::tw_off(2), tid), pw);
+    twiddle_powers<8>(base_twiddle<-1>(a.tw16, S::tw_off(2), tid + T), pw + 8);
+    tm_st_f2x16(tpw + 32, pw);
   }
 
   int iv = 0, jt = 0;
@@ -300,7 +389,15 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
     }
     cp_async_commit();
     r16_first_pass<-1, float4, HALF>(buf, v, tid);
-    r16_pass_range<-1, LOGN, 1, S::NPASS, float4, true>(buf, a.tw16, tid);   // natural, unswizzled
+    {
+      tm_wait_st();                             // the powers (and the zeroed sums) are stored
+      float2 pw[16];
+      tm_ld_f2x16(tpw, pw);
+      r16_pass<-1, N, 16, float4, false, true>(buf, S::ns(1), a.tw16, S::tw_off(1), tid, pw);
+      tm_ld_f2x16(tpw + 32, pw);
+      // the last pass leaves its natural-order output unswizzled
+      r16_pass<-1, N, 8, float4, true, true>(buf, S::ns(2), a.tw16, S::tw_off(2), tid, pw);
+    }
     cp_async_wait_all_but_1();                  // taps of panel p
     __syncthreads();
     tm_wait_st();                               // the previous panel's sums are in TMEM
@@ -359,7 +456,7 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(*tslot),
-                 "r"((uint32_t)kTmCols));
+                 "r"((uint32_t)(2 * kTmCols)));
   }
 #pragma unroll
   for (int s = 0; s < 16; ++s) acc[s] = cscale(acc[s], __ldg(a.wt + tid + T * s));
@@ -404,8 +501,8 @@ template <int LOGN, bool SHIFT, bool HALF>
 cudaError_t launch_adj16_h(const RowArgs& a, cudaStream_t s) {
   constexpr int N = 1 << LOGN;
   static bool attr = false;
-  const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.atab_ld * sizeof(uint2);
-  cudaError_t e = set_smem(stolt_adj_rows16<LOGN, SHIFT, HALF>, smem_cap<LOGN>(false), attr);
+  const size_t smem = (size_t)2 * N * sizeof(float4) + (size_t)a.atab_ld * sizeof(uint2) + 16;
+  cudaError_t e = set_smem(stolt_adj_rows16<LOGN, SHIFT, HALF>, smem_cap<LOGN>(false) + 16, attr);
   if (e != cudaSuccess) return e;
   stolt_adj_rows16<LOGN, SHIFT, HALF><<<dim3(a.Lh, (a.batch + 1) / 2), N / 16, smem, s>>>(a);
   return cudaGetLastError();

@@ -139,6 +139,33 @@ __device__ __forceinline__ void twiddle16_r(E* v, float2 w) {
   }
 }
 
+// The powers w^1 .. w^(R-1) (p[r], p[0] unused) formed by exactly the
+// products twiddle16_r (R = 16) and twiddle_r (R = 8) form, so that applying
+// them with twiddle_apply gives the same values bit for bit.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 w, float2* p) {
+  static_assert(R == 8 || R == 16, "radix 8 or 16");
+  const float2 w2 = cmul(w, w), w4 = cmul(w2, w2), w3 = cmul(w2, w);
+  p[1] = w;
+  p[2] = w2;
+  p[3] = w3;
+  p[4] = w4;
+  p[5] = cmul(w4, w);
+  p[6] = cmul(w4, w2);
+  p[7] = cmul(w4, w3);
+  if constexpr (R == 16) {
+    const float2 w8 = cmul(w4, w4);
+    p[8] = w8;
+#pragma unroll
+    for (int r = 1; r < 8; ++r) p[8 + r] = cmul(w8, p[r]);
+  }
+}
+template <int R, typename E>
+__device__ __forceinline__ void twiddle_apply(E* v, const float2* p) {
+#pragma unroll
+  for (int r = 1; r < R; ++r) v[r] = cmul(v[r], p[r]);
+}
+
 // Radix schedule of a length 2^LOGN transform: radix 16 while four or more
 // factors of two remain, then one radix 2, 4 or 8 pass.
 template <int LOGN>
@@ -174,10 +201,12 @@ __host__ __device__ constexpr bool swz16_shift_free(int c) {
 }
 
 // One in-place Stockham pass, T = N/16 threads, each with 16 / R butterflies
-// of radix R; PLAIN_OUT as in row_pass (common.cuh).
-template <int DIR, int N, int R, typename E, bool PLAIN_OUT = false>
+// of radix R; PLAIN_OUT as in row_pass (common.cuh).  PW: the twiddle powers
+// of the thread's butterflies are given, butterfly q's power r at pw[q R + r]
+// (see twiddle_powers), instead of formed from tw.
+template <int DIR, int N, int R, typename E, bool PLAIN_OUT = false, bool PW = false>
 __device__ __forceinline__ void r16_pass(E* buf, int Ns, const float2* __restrict__ tw, int off,
-                                         int tid) {
+                                         int tid, const float2* pw = nullptr) {
   constexpr int T = N / 16, NB = 16 / R;
   constexpr bool rd_lin = swz16_shift_free<E>(N / R);   // jb < N/R
   E v[16];
@@ -196,7 +225,8 @@ __device__ __forceinline__ void r16_pass(E* buf, int Ns, const float2* __restric
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
     const int k = jb & (Ns - 1);
-    if (Ns > 1) twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, off, k));
+    if constexpr (PW) twiddle_apply<R>(&v[q * R], pw + q * R);
+    else if (Ns > 1) twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, off, k));
     dft16_r<DIR, R>(&v[q * R]);
     const int base = (jb - k) * R + k;
     const int bases = PLAIN_OUT ? base : swz16<E>(base);
@@ -235,11 +265,13 @@ __device__ __forceinline__ void r16_first_pass(E* buf, E* v, int tid) {
 // Last pass read from shared memory and stored to the global rows outA / outB
 // (outB may be null; unused for float2), keeping outputs with index < n_keep.
 // Ns = N/R > jb, so output r of butterfly jb is element jb + r Ns.  KEEP_LOW:
-// n_keep <= N/2, so outputs r >= R/2 (elements >= N/2) are not formed.
-template <int DIR, int LOGN, typename E, bool KEEP_LOW = false>
+// n_keep <= N/2, so outputs r >= R/2 (elements >= N/2) are not formed.  PW
+// as in r16_pass.
+template <int DIR, int LOGN, typename E, bool KEEP_LOW = false, bool PW = false>
 __device__ __forceinline__ void r16_last_pass_global(const E* buf, const float2* __restrict__ tw,
                                                      int tid, float2* __restrict__ outA,
-                                                     float2* __restrict__ outB, int n_keep) {
+                                                     float2* __restrict__ outB, int n_keep,
+                                                     const float2* pw = nullptr) {
   using S = Sched16<LOGN>;
   constexpr int Q = S::NPASS - 1, R = S::radix(Q), N = S::N, T = N / 16, NB = 16 / R;
   constexpr int Ns = S::ns(Q);
@@ -256,7 +288,8 @@ __device__ __forceinline__ void r16_last_pass_global(const E* buf, const float2*
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int jb = tid + T * q;
-    twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, S::tw_off(Q), jb));
+    if constexpr (PW) twiddle_apply<R>(&v[q * R], pw + q * R);
+    else twiddle16_r<R>(&v[q * R], base_twiddle<DIR>(tw, S::tw_off(Q), jb));
     dft16_r<DIR, R>(&v[q * R]);
 #pragma unroll
     for (int r = 0; r < (KEEP_LOW ? R / 2 : R); ++r) {

@@ -62,6 +62,8 @@ def test_autotune_choice_and_cache(lib, tmp_path):
     (400, 30, [1500.0, 2300.0], [0.0, 0.05], 2, False,
      dict(wavelet_peak_hz=25.0, fmax_hz=90.0)),                               # Nt 1024, AASHRT + C
     (1024, 17, [0.0, 2500.0], None, 1, False, dict(pad_t=4)),                 # Nt 4096, v = 0, pad 4
+    (700, 20, [1600.0, 2500.0], [0.0, 0.03], 1, True,
+     dict(wavelet_peak_hz=25.0)),                                             # Nt 2048, AASHRT, one gather
 ])
 def test_radix16_rows_match_oracle(lib, nt, nx, v, t0, batch, mask, kw):
     """The radix-16 row kernels on every length they serve, in both CTA
