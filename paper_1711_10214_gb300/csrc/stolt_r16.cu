@@ -244,10 +244,15 @@ stolt_adj_rows16(RowArgs a) {
     r16_first_pass<-1>(buf, v, tid);
   }
   r16_pass_range<-1, LOGN, 1, S::NPASS, float4, true>(buf, a.tw16, tid);
+  // With asymptote shifts the data spectrum is kept multiplied by the
+  // conjugate phase of the current shift (shift 0 here, then moved on each
+  // time the shift changes), so the gathers need no per-source phase.
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
     const int k = tid + T * s;
-    dsp[k] = cscale(buf[k], __ldg(a.wt + k));   // natural order, unswizzled
+    float4 dk = cscale(buf[k], __ldg(a.wt + k));   // natural order, unswizzled
+    if (SHIFT) dk = cmul(dk, cconj(__ldg(a.phase + k)));
+    dsp[k] = dk;
   }
 
   float2* xA = a.Xw + (long long)b0 * a.x_batch + (long long)l * a.ld;
@@ -257,16 +262,27 @@ stolt_adj_rows16(RowArgs a) {
   for (int p = 0; p < a.P; ++p) {
     cp_async_wait_all();
     __syncthreads();
+    if (SHIFT && iv == 0 && p > 0) {
+      // shift jt - 1 -> jt: each thread moves the bins it wrote, after every
+      // gather of the previous panel (the barrier above) and before the next
+      const float2* ph1 = a.phase + (long long)jt * N;
+      const float2* ph0 = ph1 - N;
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        const int k = tid + T * s;
+        dsp[k] = cmul(dsp[k], cmul(cconj(__ldg(ph1 + k)), __ldg(ph0 + k)));
+      }
+      __syncthreads();
+    }
     const bool mapped = km < H;
     // the next panel's, loaded a panel ahead of its use
     if (p + 1 < a.P) km = __ldg(a.kmin + (iv + 1 == a.nv ? 0 : iv + 1) * a.Lh + l);
-    const float2* phj = SHIFT ? a.phase + (long long)jt * N : nullptr;
     float4 accs[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s)
-      accs[s] = mapped ? adj_gather_bin<N, 0, SHIFT>(dsp, stab, tid + T * s, phj, s < 8)
+      accs[s] = mapped ? adj_gather_bin<N, 0, false>(dsp, stab, tid + T * s, nullptr, s < 8)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tid == 0 && mapped) accs[0] = adj_gather_bin0_mirror<N, 0, SHIFT>(dsp, stab, phj, accs[0]);
+    if (tid == 0 && mapped) accs[0] = adj_gather_bin0_mirror<N, 0, false>(dsp, stab, nullptr, accs[0]);
     // its barrier also ends every thread's reads of the source-table row
     r16_first_pass<+1>(buf, accs, tid);
     if (p + 1 < a.P) {
@@ -314,7 +330,12 @@ stolt_adj_rows16(RowArgs a) {
 // warps.  TMEM per CTA: 128 columns, the sums in 0..63 and the twiddle powers
 // of the thread's butterflies (they depend on the thread and the pass, not on
 // the panel: formed once, by the products the passes would form) in 64..127;
-// four CTAs, the most that fit an SM, hold its 512 columns.  cp.async groups, in commit order: rows of panel p, taps of
+// four CTAs, the most that fit an SM, hold its 512 columns.  With asymptote
+// shifts (panels p = j nv + i) the sums are kept in the phase frame of the
+// current shift j, S_j = sum_{j' <= j} (phi_j' / phi_j) A_j', A_j' the
+// unphased sum over shift j''s velocities and phi_j = exp(-i w tau0_j): each
+// panel adds its map without a phase, the sums turn by phi_{j-1} conj(phi_j)
+// when j changes, and by phi_{last} at the end.  cp.async groups, in commit order: rows of panel p, taps of
 // panel p, rows of p + 1, taps of p + 1, ... (a group may be empty), so
 // "all but the newest group complete" is the rows at the start of a panel and
 // the taps before its map.
@@ -415,10 +436,25 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
         if (t.valid) {
           vk[j] = cscale(buf[t.i0], t.w0);
           vk[j] = cfma(t.w1, buf[t.i1], vk[j]);
-          if (SHIFT) vk[j] = cmul(vk[j], __ldg(a.phase + (long long)jt * N + k));
         }
       }
       tm_wait_ld(r);
+      if (SHIFT && iv == 0 && p > 0) {
+        // shift jt - 1 -> jt: the sums move to the new shift's phase frame
+        const float2* ph1 = a.phase + (long long)jt * N;
+        const float2* ph0 = ph1 - N;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = tid + T * (4 * c + j);
+          float4 sk = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                  __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          sk = cmul(sk, cmul(__ldg(ph0 + k), cconj(__ldg(ph1 + k))));
+          r[4 * j] = __float_as_uint(sk.x);
+          r[4 * j + 1] = __float_as_uint(sk.y);
+          r[4 * j + 2] = __float_as_uint(sk.z);
+          r[4 * j + 3] = __float_as_uint(sk.w);
+        }
+      }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         r[4 * j] = __float_as_uint(__uint_as_float(r[4 * j]) + vk[j].x);
@@ -458,8 +494,14 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(*tslot),
                  "r"((uint32_t)(2 * kTmCols)));
   }
+  // with asymptote shifts the sums are in the last shift's phase frame
+  const float2* phl = SHIFT ? a.phase + (long long)(a.nt0 - 1) * N : nullptr;
 #pragma unroll
-  for (int s = 0; s < 16; ++s) acc[s] = cscale(acc[s], __ldg(a.wt + tid + T * s));
+  for (int s = 0; s < 16; ++s) {
+    const int k = tid + T * s;
+    if (SHIFT) acc[s] = cmul(acc[s], __ldg(phl + k));
+    acc[s] = cscale(acc[s], __ldg(a.wt + k));
+  }
   r16_first_pass<+1>(buf, acc, tid);
   r16_pass_range<+1, LOGN, 1, S::NPASS - 1>(buf, a.tw16, tid);
   float2* yA = a.Yw + (long long)b0 * a.y_batch + (long long)l * a.ld;

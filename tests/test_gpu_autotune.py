@@ -64,6 +64,8 @@ def test_autotune_choice_and_cache(lib, tmp_path):
     (1024, 17, [0.0, 2500.0], None, 1, False, dict(pad_t=4)),                 # Nt 4096, v = 0, pad 4
     (700, 20, [1600.0, 2500.0], [0.0, 0.03], 1, True,
      dict(wavelet_peak_hz=25.0)),                                             # Nt 2048, AASHRT, one gather
+    (600, 24, [1700.0, 2600.0], [0.0, 0.02, 0.05, 0.07, 0.11], 2, False,
+     dict(wavelet_peak_hz=25.0)),                                             # Nt 2048, 5 uneven shifts
 ])
 def test_radix16_rows_match_oracle(lib, nt, nx, v, t0, batch, mask, kw):
     """The radix-16 row kernels on every length they serve, in both CTA
