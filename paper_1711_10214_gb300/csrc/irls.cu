@@ -296,14 +296,39 @@ __global__ void k_wm(float* __restrict__ m, float* __restrict__ wminv, float* __
   const long long off = (long long)g * n;
   const float e = (float)scal[S_EPSM * B + g];
   const bool active = scal[S_ACTIVE * B + g] != 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float mv = m[off + i];
+  auto weight = [&](float mv) {
     float w = 1.f;
     if (e > 0.f) {
       const float a = fmaxf(fabsf(mv), e);
       w = (q == 2.f) ? 1.f : (q == 1.f) ? sqrtf(a) : powf(a, 0.5f * (2.f - q));
     }
+    return w;
+  };
+  if (!amask && (n & 3) == 0) {
+    // four elements per thread and iteration: enough loads in flight to
+    // stream the model at the memory's rate (the vectors are 16-byte aligned:
+    // n is a multiple of 4 and the buffers are)
+    float4* m4 = (float4*)(m + off);
+    float4* w4 = (float4*)(wminv + off);
+    float4* u4 = u ? (float4*)(u + off) : nullptr;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n / 4;
+         i += (long long)gridDim.x * blockDim.x) {
+      const float4 mv = m4[i];
+      const float4 w = make_float4(weight(mv.x), weight(mv.y), weight(mv.z), weight(mv.w));
+      w4[i] = w;
+      if (u4) {
+        u4[i] = make_float4(warm ? mv.x / w.x : 0.f, warm ? mv.y / w.y : 0.f,
+                            warm ? mv.z / w.z : 0.f, warm ? mv.w / w.w : 0.f);
+      } else if (active) {
+        if (!warm) m4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    return;
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float mv = m[off + i];
+    float w = weight(mv);
     if (amask && __ldg(amask + (long long)g * nx + (i / nt) % nx) == 0.f) w = 0.f;
     wminv[off + i] = w;
     if (u) u[off + i] = (warm && w != 0.f) ? mv / w : 0.f;
