@@ -106,16 +106,23 @@ def xfft_model_bytes(kernel, B, nt=NT, nx=NX, P=NV, Nx=512, n_outer=None, n_cg=N
     """Algorithmic HBM bytes of the model-side trace-axis launches of one
     deblend step (mu = 0, fused CG path), averaged per launch: the FP32 model-
     sized streams each launch must move once and the half spectrum X it writes
-    or reads.  Per outer iteration: r2c = n_cg CG forwards (the first reads
-    p~, s~ and m and writes p~ and X: its deferred m update has no alpha yet;
-    the others also write m) + 1 plain reconstruction forward (reads m,
-    writes X); c2r = n_cg weighted adjoints (reads X and W_m^-1, writes s~)."""
+    or reads.  Per outer iteration the r2c runs n_cg CG forwards and one
+    plain reconstruction forward (reads m, writes X).  CG forward it reads
+    p~_{it-1} and s~ and writes p~_it and X; the model takes its updates two
+    at a time on odd iterations, which also read and write m and, from it = 3
+    on, read p~_{it-2}.  The c2r runs n_cg weighted adjoints (reads X and
+    W_m^-1, writes s~)."""
     n_outer = N_OUTER if n_outer is None else n_outer
     n_cg = N_CG if n_cg is None else n_cg
     S = 4.0 * nx * nt * P                       # one model-sized FP32 stream, per gather
     X = 8.0 * (Nx // 2 + 1) * nt * P            # the half spectrum, per gather
     if kernel == "xfft_r2c":
-        per_outer = (4 * S + X) + (n_cg - 1) * (5 * S + X) + (S + X)
+        per_outer = S + X
+        for it in range(n_cg):
+            streams = 3                                  # p~_{it-1}, s~ in; p~_it out
+            if it & 1:
+                streams += 2 + (1 if it >= 3 else 0)     # m in and out; p~_{it-2} in
+            per_outer += streams * S + X
         launches = n_cg + 1
     else:
         per_outer = n_cg * (X + 2 * S)

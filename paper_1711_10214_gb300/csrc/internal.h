@@ -29,15 +29,21 @@ struct XfftArgs {
   int slabs = 0;
   int cols = 16;                     // complex time columns per CTA: 16 or 8 (Nx <= 512)
   // r2c only: a CGLS vector update fused into the input load (the solver's
-  // mu = 0 path).  Per gather g, coef[g] = (cs, beta, alpha, -):
-  //   mode 1 (model side): x = cs s + beta p; p <- x; u <- u + alpha p_old
+  // mu = 0 path).  Per gather g, coef[g] = (cs, beta, alpha, alpha2):
+  //   mode 1 (model side): x = cs s + beta p; p_out <- x;
+  //                        u <- u + alpha p (+ alpha2 p2 when cg_p2_read)
   //   mode 2 (data side):  x = r - alpha q;  r <- x
-  // where p (mode 1) or r (mode 2) is in_real, read and written in place,
-  // and x is then transformed.
+  // where p (mode 1) or r (mode 2) is in_real, and x is then transformed.
+  // p_out is cg_pout, or in_real itself (in place) when cg_pout is null; p2
+  // (read only when cg_p2_read) is the same buffer as cg_pout: a p two
+  // iterations old whose elements are read before x overwrites them.
   int cg_mode = 0;
-  float* cg_io = nullptr;            // == in_real, written
+  float* cg_io = nullptr;            // == in_real
   const float* cg_s = nullptr;       // s (mode 1) or q (mode 2)
   float* cg_u = nullptr;             // u (mode 1)
+  float* cg_pout = nullptr;          // mode 1: where x is written (null: in place)
+  int cg_p2_read = 0;                // mode 1: add alpha2 p2, p2 read from cg_pout
+  int cg_u_rw = 1;                   // mode 1: u is updated (0: u is neither read nor written)
   const float4* cg_coef = nullptr;   // [gathers]
   int tma = 1;                       // r2c: use the persistent TMA kernel where it applies
   int* err = nullptr;                // set to 1 if a bounded device wait ran out
@@ -50,7 +56,10 @@ struct CgFuse {
                                      // once more (W_m^-2 L^T ..., the CG's s~ = W_m^-1 s)
   const float* s = nullptr;          // s (mode 1) or q (mode 2)
   float* u = nullptr;                // u (mode 1)
-  const float4* coef = nullptr;      // per gather (cs, beta, alpha, -)
+  float* pout = nullptr;             // mode 1: the new p's buffer (null: in place)
+  int p2_read = 0;                   // mode 1: also add alpha2 times the p held in pout
+  int u_rw = 1;                      // mode 1: this launch updates u (0: u untouched)
+  const float4* coef = nullptr;      // per gather (cs, beta, alpha, alpha2)
 };
 
 // Arguments of the fused t-FFT + Stolt map + sum/spray row kernels.

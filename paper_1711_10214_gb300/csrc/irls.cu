@@ -417,12 +417,18 @@ __global__ void k_cg_coef_fwd(const double* scal, int B, int it, float4* coef) {
     coef[g] = make_float4(1.f, 0.f, 0.f, 0.f);
     return;
   }
+  const float4 prev = coef[g];
   const double gprev = scal[(S_GAM0 + ((it - 1) & 1)) * B + g];
   const double gcur = scal[(S_GAM0 + (it & 1)) * B + g];
   const bool act = scal[S_ACTIVE * B + g] != 0.0 && gprev > 0.0;
   const float alpha = (float)cg_alpha(scal, B, g, it - 1);
-  coef[g] = act ? make_float4(1.f, (float)(gcur / gprev), alpha, 0.f)
-                : make_float4(0.f, 1.f, alpha, 0.f);
+  // the model takes its updates two at a time, on odd iterations:
+  // alpha_{it-1} p~_{it-1} + alpha_{it-2} p~_{it-2}; an even iteration only
+  // keeps its alpha_{it-1} (in .w, where the next one finds it)
+  const float az = (it & 1) ? alpha : 0.f;
+  const float aw = (it & 1) ? (it >= 3 ? prev.w : 0.f) : alpha;
+  coef[g] = act ? make_float4(1.f, (float)(gcur / gprev), az, aw)
+                : make_float4(0.f, 1.f, az, aw);
 }
 
 // Adjoint of iteration it: r -= alpha_it q_it.
@@ -432,16 +438,20 @@ __global__ void k_cg_coef_adj(const double* scal, int B, int it, float4* coef) {
   coef[g] = make_float4(0.f, 0.f, (float)cg_alpha(scal, B, g, it), 0.f);
 }
 
-// u += alpha_it p (the last CGLS iteration's model update)
-__global__ void k_upd_u(float* __restrict__ u, const float* __restrict__ p, long long nm,
-                        const double* scal, int B, int it) {
+// The model updates still deferred after the last CGLS iteration it:
+// u += alpha_it p, and after an even it also the one kept from it - 1,
+// alpha_{it-1} pprev (alpha_{it-1} in the forward coefficients' .w).
+__global__ void k_upd_u2(float* __restrict__ u, const float* __restrict__ p,
+                         const float* __restrict__ pprev, long long nm, const double* scal, int B,
+                         int it, const float4* __restrict__ coef) {
   const int g = blockIdx.y;
   const float a = (float)cg_alpha(scal, B, g, it);
-  if (a == 0.f) return;
+  const float a2 = (it & 1) ? 0.f : coef[g].w;
+  if (a == 0.f && a2 == 0.f) return;
   const long long om = (long long)g * nm;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nm;
        i += (long long)gridDim.x * blockDim.x)
-    u[om + i] = fmaf(a, p[om + i], u[om + i]);
+    u[om + i] = fmaf(a, p[om + i], fmaf(a2, pprev[om + i], u[om + i]));
 }
 
 // p = s at the start of CGLS; delta_0 = mu ||p||^2
@@ -692,22 +702,30 @@ ashrt_status robust_irls_deblend(const ashrt_plan* P, const float* d, float* m, 
         // weight.  The forward of iteration it forms p~_it = s~_it + beta
         // p~_{it-1} and applies the deferred m += alpha_{it-1} p~_{it-1}; the
         // adjoint forms r -= alpha_it q_it and returns s~ = W_m^-2 L^T (..) with
-        // gamma = ||W_m^-1 L^T (..)||^2.  The last iteration's m update runs on
-        // its own.
+        // gamma = ||W_m^-1 L^T (..)||^2.  The model takes its deferred updates
+        // two at a time (odd iterations: alpha_{it-1} p~_{it-1} +
+        // alpha_{it-2} p~_{it-2}), so p~ alternates between two buffers (the
+        // unweighted path's u is free here): iteration it reads p~_{it-1} and
+        // writes p~_it over p~_{it-2}, after reading it when it is odd.  What
+        // is still deferred after the last iteration runs on its own.
         float4* cf_f = P->cg_coef;
         float4* cf_a = P->cg_coef + B;
+        float* const pb[2] = {P->pv, P->u};     // p~_it in pb[it & 1]
         for (int it = 0; it < o.n_cg; ++it) {
           LAUNCH(k_cg_coef_fwd, (B + 127) / 128, 128, scal, B, it, cf_f);
           CgFuse ff;
           ff.mode = 1;
           ff.s = P->sv;
           ff.u = m;
+          ff.pout = pb[it & 1];
+          ff.p2_read = (it & 1) && it >= 3;
+          ff.u_rw = it & 1;                     // even iterations leave the model alone
           ff.coef = cf_f;
-          CK(op_forward(P, P->pv, P->qv, nullptr, P->wr, tm, scal + (S_DEL0 + (it & 1)) * B, B,
-                        s, &ff));
+          CK(op_forward(P, pb[(it + 1) & 1], P->qv, nullptr, P->wr, tm,
+                        scal + (S_DEL0 + (it & 1)) * B, B, s, &ff));
           ++applies_f;
           if (it + 1 == o.n_cg) {
-            LAUNCH(k_upd_u, gm, kThreads, m, P->pv, nm, scal, B, it);
+            LAUNCH(k_upd_u2, gm, kThreads, m, pb[it & 1], pb[(it + 1) & 1], nm, scal, B, it, cf_f);
             break;
           }
           LAUNCH(k_cg_coef_adj, (B + 127) / 128, 128, scal, B, it, cf_a);

@@ -200,6 +200,9 @@ cudaError_t op_forward(const ashrt_plan* p, const float* m, float* d, const floa
     ax.cg_io = const_cast<float*>(m);
     ax.cg_s = cg->s;
     ax.cg_u = cg->u;
+    ax.cg_pout = cg->pout;
+    ax.cg_p2_read = cg->p2_read;
+    ax.cg_u_rw = cg->u_rw;
     ax.cg_coef = cg->coef;
   }
   prof_begin(PROF_XR2C, s);
@@ -573,6 +576,13 @@ static ashrt_status plan_create_impl(ashrt_plan** out, int nt, int nx, double dt
     // the padding columns of the spectra rows are never written: keep them zero
     cudaError_t e = cudaMemset(p->X, 0, B * p->P * xpan * sizeof(float2));
     if (e == cudaSuccess) e = cudaMemset(p->Y, 0, B * xpan * sizeof(float2));
+    // the CG's two direction buffers enter the first update times beta = 0:
+    // they must hold finite values from the start
+    if (e == cudaSuccess && p->with_solver) {
+      const size_t me = B * model_elems(p);
+      e = cudaMemset(p->pv, 0, me * sizeof(float));
+      if (e == cudaSuccess) e = cudaMemset(p->u, 0, me * sizeof(float));
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) st = cuda_fail(e, "plan_create workspace init");
   }

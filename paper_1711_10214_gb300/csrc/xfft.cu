@@ -118,16 +118,24 @@ __device__ __forceinline__ float2 cg_update_pair(const XfftArgs& a, long long of
   const float2 y = ld_pair(a.cg_s + off, t, a.nt, vec);
   float2 z;
   if (a.cg_mode == 1) {
+    float* po = a.cg_pout ? a.cg_pout + off : io;
     z = make_float2(fmaf(cf.x, y.x, cf.y * x.x), fmaf(cf.x, y.y, cf.y * x.y));
-    if (cf.z != 0.f) {
+    const bool two = a.cg_p2_read && cf.w != 0.f;
+    if (a.cg_u_rw && (cf.z != 0.f || two)) {
       float* u = a.cg_u + off;
-      const float2 uo = ld_pair(u, t, a.nt, vec);
-      st_pair(u, t, a.nt, vec, make_float2(fmaf(cf.z, x.x, uo.x), fmaf(cf.z, x.y, uo.y)));
+      float2 un = ld_pair(u, t, a.nt, vec);
+      if (two) {
+        const float2 p2 = ld_pair(po, t, a.nt, vec);   // read before z overwrites it
+        un = make_float2(fmaf(cf.w, p2.x, un.x), fmaf(cf.w, p2.y, un.y));
+      }
+      un = make_float2(fmaf(cf.z, x.x, un.x), fmaf(cf.z, x.y, un.y));
+      st_pair(u, t, a.nt, vec, un);
     }
+    st_pair(po, t, a.nt, vec, z);
   } else {
     z = make_float2(fmaf(-cf.z, y.x, x.x), fmaf(-cf.z, y.y, x.y));
+    st_pair(io, t, a.nt, vec, z);
   }
-  st_pair(io, t, a.nt, vec, z);
   return z;
 }
 
@@ -216,7 +224,7 @@ xfft_r2c_kernel(XfftArgs a) {
 // Requires nx <= 256 (one box per vector), nt % 4 == 0 and 16-byte aligned
 // vectors; the launcher falls back to xfft_r2c_kernel otherwise.
 struct R2cMaps {
-  CUtensorMap in, s, u, w;
+  CUtensorMap in, s, u, w, p2;   // p2: the new p's buffer (cg_pout), also read when cg_p2_read
 };
 
 template <int LOGN>
@@ -230,11 +238,16 @@ xfft_r2c_tma(XfftArgs a, const __grid_constant__ R2cMaps mp, int n_tt, long long
   const bool has_w = a.ew != nullptr;
   const int box = a.nx * 16;                          // floats of one vector's box
   const int slot = (box * 4 + 127) & ~127;            // bytes, 128-byte aligned
-  const int i_s = 1, i_u = mode ? 2 : 1, i_w = mode == 1 ? 3 : (mode ? 2 : 1);
-  const int nslot = 1 + (mode ? 1 : 0) + (mode == 1 ? 1 : 0) + (has_w ? 1 : 0);
+  const bool p2r = mode == 1 && a.cg_p2_read;
+  const bool urw = mode == 1 && a.cg_u_rw;
+  const bool pout = mode == 1 && a.cg_pout != nullptr;
+  const int i_s = 1, i_u = 2, i_p2 = urw ? 3 : 2;
+  const int i_w = 1 + (mode ? 1 : 0) + (urw ? 1 : 0) + (p2r ? 1 : 0);
+  const int nslot = i_w + (has_w ? 1 : 0);
   float* st_in = (float*)base;
   float* st_s = (float*)(base + i_s * slot);
   float* st_u = (float*)(base + i_u * slot);
+  float* st_p2 = (float*)(base + i_p2 * slot);
   float* st_w = (float*)(base + i_w * slot);
   float2* sm = (float2*)(base + nslot * slot);        // [N][C]
   uint64_t* bar = (uint64_t*)(sm + N * C);
@@ -250,7 +263,8 @@ xfft_r2c_tma(XfftArgs a, const __grid_constant__ R2cMaps mp, int n_tt, long long
     mbar_arrive_expect_tx(bar, (uint32_t)(nslot * box * 4));
     tma_load_3d(st_in, &mp.in, x, 0, z, bar);
     if (mode) tma_load_3d(st_s, &mp.s, x, 0, z, bar);
-    if (mode == 1) tma_load_3d(st_u, &mp.u, x, 0, z, bar);
+    if (urw) tma_load_3d(st_u, &mp.u, x, 0, z, bar);
+    if (p2r) tma_load_3d(st_p2, &mp.p2, x, 0, z, bar);
     if (has_w) tma_load_3d(st_w, &mp.w, x, 0, z, bar);
   };
   long long tile = blockIdx.x;
@@ -286,9 +300,14 @@ xfft_r2c_tma(XfftArgs a, const __grid_constant__ R2cMaps mp, int n_tt, long long
           float2 x = *(const float2*)(st_in + e);
           if (mode == 1) {
             const float2 sv = *(const float2*)(st_s + e);
-            if (cf.z != 0.f) {
-              const float2 uo = *(const float2*)(st_u + e);
-              *(float2*)(st_u + e) = make_float2(fmaf(cf.z, x.x, uo.x), fmaf(cf.z, x.y, uo.y));
+            const bool two = p2r && cf.w != 0.f;
+            if (urw && (cf.z != 0.f || two)) {
+              float2 un = *(const float2*)(st_u + e);
+              if (two) {
+                const float2 p2 = *(const float2*)(st_p2 + e);
+                un = make_float2(fmaf(cf.w, p2.x, un.x), fmaf(cf.w, p2.y, un.y));
+              }
+              *(float2*)(st_u + e) = make_float2(fmaf(cf.z, x.x, un.x), fmaf(cf.z, x.y, un.y));
             }
             x = make_float2(fmaf(cf.x, sv.x, cf.y * x.x), fmaf(cf.x, sv.y, cf.y * x.y));
             *(float2*)(st_in + e) = x;
@@ -323,8 +342,9 @@ xfft_r2c_tma(XfftArgs a, const __grid_constant__ R2cMaps mp, int n_tt, long long
     __syncthreads();
     if (tid == 0) {
       if (mode) {
-        tma_store_3d(&mp.in, t0, 0, (int)slab, st_in);
-        if (mode == 1 && cf.z != 0.f) tma_store_3d(&mp.u, t0, 0, (int)slab, st_u);
+        tma_store_3d(pout ? &mp.p2 : &mp.in, t0, 0, (int)slab, st_in);
+        if (urw && (cf.z != 0.f || (p2r && cf.w != 0.f)))
+          tma_store_3d(&mp.u, t0, 0, (int)slab, st_u);
         bulk_commit();
         bulk_wait_read();
       }
@@ -537,8 +557,14 @@ cudaError_t launch_r2c_tma(const XfftArgs& a, cudaStream_t s, bool* used) {
   if (mode && !encode_tmap_f32_3d(&mp.s, a.cg_s, a.nt, a.nx, slabs, 16, a.nx)) return cudaSuccess;
   if (mode == 1 && !encode_tmap_f32_3d(&mp.u, a.cg_u, a.nt, a.nx, slabs, 16, a.nx))
     return cudaSuccess;
+  if (mode == 1 && a.cg_pout &&
+      !encode_tmap_f32_3d(&mp.p2, a.cg_pout, a.nt, a.nx, slabs, 16, a.nx))
+    return cudaSuccess;
   if (a.ew && !encode_tmap_f32_3d(&mp.w, a.ew, a.nt, a.nx, slabs, 16, a.nx)) return cudaSuccess;
-  const int nslot = 1 + (mode ? 1 : 0) + (mode == 1 ? 1 : 0) + (a.ew ? 1 : 0);
+  const bool p2r = mode == 1 && a.cg_p2_read;
+  const bool urw = mode == 1 && a.cg_u_rw;
+  if (p2r && (!a.cg_pout || !urw)) return cudaErrorInvalidValue;
+  const int nslot = 1 + (mode ? 1 : 0) + (urw ? 1 : 0) + (p2r ? 1 : 0) + (a.ew ? 1 : 0);
   const size_t slot = ((size_t)a.nx * 64 + 127) & ~(size_t)127;
   const size_t smem = 128 + nslot * slot + (size_t)N * C * sizeof(float2) + 16;
   static int max_smem_set = 0;
