@@ -5,7 +5,7 @@ outer iteration, ch. 4).  Here a U-Net (``ashrt_unet_*`` in the library)
 learns, from pairs the cold solve itself produces, to map a pseudo-deblended
 gather to (a) an initial Radon model m0 and (b) initial residual weights W_r0;
 the solve then starts from them (``irls_opts.m0_dev`` / ``wr0_dev``).  The cold
-solve stays the reference: the warm start is judged by the operator applies
+solve stays the reference: the warm start is measured by the operator applies
 and gathers/s it needs to reach the cold solve's deblending quality within a
 stated margin (0.1 dB of Q).
 
