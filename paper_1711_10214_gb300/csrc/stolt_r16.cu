@@ -324,7 +324,7 @@ stolt_adj_rows16(RowArgs a) {
 // Forward rows for Nt = 2048 with the accumulator in tensor memory: as
 // stolt_fwd_rows16<11>, but each thread's 16 accumulated bins live in TMEM
 // instead of 64 registers, and the tap row is single-buffered (staged at the
-// end of a panel, waited for before the next map), so that 128 registers and
+// start of a panel, waited for before its map), so that 128 registers and
 // 53 KB of shared memory per CTA let four CTAs share an SM instead of three:
 // the kernel is issue-bound and hides its shared-memory latency with the extra
 // warps.  TMEM per CTA: 128 columns, the sums in 0..63 and the twiddle powers
@@ -335,10 +335,11 @@ stolt_adj_rows16(RowArgs a) {
 // current shift j, S_j = sum_{j' <= j} (phi_j' / phi_j) A_j', A_j' the
 // unphased sum over shift j''s velocities and phi_j = exp(-i w tau0_j): each
 // panel adds its map without a phase, the sums turn by phi_{j-1} conj(phi_j)
-// when j changes, and by phi_{last} at the end.  cp.async groups, in commit order: rows of panel p, taps of
-// panel p, rows of p + 1, taps of p + 1, ... (a group may be empty), so
-// "all but the newest group complete" is the rows at the start of a panel and
-// the taps before its map.
+// when j changes, and by phi_{last} at the end.  cp.async groups, in commit order: rows of panel p (issued
+// during panel p - 1), taps of panel p (issued after panel p's first barrier,
+// which ends every read of panel p - 1), rows of p + 1 (a group may be
+// empty): a panel starts once all have landed, and its map once all but the
+// newest have (the wait rides on the last transform pass's closing barrier).
 template <bool SHIFT, bool HALF>
 __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
   constexpr int LOGN = 11, N = 1 << LOGN, T = N / 16;
@@ -355,8 +356,6 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
   const unsigned* trow = a.taps + (long long)l * a.taps_ld;
   const long long tstep = (long long)a.Lh * a.taps_ld;
   stage_rows(stage, xA, xB, a.ld, tid, T);
-  cp_async_commit();
-  stage_taps(stap, trow, a.taps_ld, tid, T);
   cp_async_commit();
 
   if (warp == 0) {
@@ -389,8 +388,12 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
 
   int iv = 0, jt = 0;
   for (int p = 0; p < a.P; ++p) {
-    cp_async_wait_all_but_1();                  // rows of panel p
+    // rows of panel p landed; every read of the previous panel (its map's
+    // reads of buf and of the tap row) is done, so its tap row is restaged
+    cp_async_wait_all();
     __syncthreads();
+    stage_taps(stap, trow + iv * tstep, a.taps_ld, tid, T);
+    cp_async_commit();
     float4 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -416,11 +419,11 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
       tm_ld_f2x16(tpw, pw);
       r16_pass<-1, N, 16, float4, false, true>(buf, S::ns(1), a.tw16, S::tw_off(1), tid, pw);
       tm_ld_f2x16(tpw + 32, pw);
-      // the last pass leaves its natural-order output unswizzled
-      r16_pass<-1, N, 8, float4, true, true>(buf, S::ns(2), a.tw16, S::tw_off(2), tid, pw);
+      // the last pass leaves its natural-order output unswizzled; before its
+      // closing barrier the tap row of panel p (every cp.async group but the
+      // newest, the rows of panel p + 1) has landed
+      r16_pass<-1, N, 8, float4, true, true, true>(buf, S::ns(2), a.tw16, S::tw_off(2), tid, pw);
     }
-    cp_async_wait_all_but_1();                  // taps of panel p
-    __syncthreads();
     tm_wait_st();                               // the previous panel's sums are in TMEM
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -468,12 +471,6 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
       iv = 0;
       ++jt;
     }
-    __syncthreads();                            // reads of buf and of the tap row done
-    if (p + 1 < a.P) {
-      const int ivn = iv;                         // the next panel's velocity index
-      stage_taps(stap, trow + ivn * tstep, a.taps_ld, tid, T);
-    }
-    cp_async_commit();
   }
   tm_wait_st();
   float4 acc[16];

@@ -204,7 +204,8 @@ __host__ __device__ constexpr bool swz16_shift_free(int c) {
 // of radix R; PLAIN_OUT as in row_pass (common.cuh).  PW: the twiddle powers
 // of the thread's butterflies are given, butterfly q's power r at pw[q R + r]
 // (see twiddle_powers), instead of formed from tw.
-template <int DIR, int N, int R, typename E, bool PLAIN_OUT = false, bool PW = false>
+template <int DIR, int N, int R, typename E, bool PLAIN_OUT = false, bool PW = false,
+          bool WAIT_CP1 = false>
 __device__ __forceinline__ void r16_pass(E* buf, int Ns, const float2* __restrict__ tw, int off,
                                          int tid, const float2* pw = nullptr) {
   constexpr int T = N / 16, NB = 16 / R;
@@ -236,6 +237,9 @@ __device__ __forceinline__ void r16_pass(E* buf, int Ns, const float2* __restric
       buf[PLAIN_OUT ? o : (wr_lin ? bases + r * Ns : swz16<E>(o))] = v[q * R + r];
     }
   }
+  // WAIT_CP1: the thread's cp.async groups but the newest complete before the
+  // barrier, so the copies they staged are visible after it
+  if constexpr (WAIT_CP1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
   __syncthreads();
 }
 
