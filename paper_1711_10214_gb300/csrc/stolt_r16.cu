@@ -406,13 +406,14 @@ __global__ void __launch_bounds__(128, 4) stolt_fwd_rows16_tm(RowArgs a) {
       const float2 zb = (hasB && i < a.nt) ? stage[a.ld + i] : make_float2(0.f, 0.f);
       v[r] = pack2(za, zb);
     }
-    __syncthreads();
+    // its barrier also ends every thread's reads of the staged rows, which
+    // are then restaged with the next panel's
+    r16_first_pass<-1, float4, HALF>(buf, v, tid);
     if (p + 1 < a.P) {
       const long long o = (long long)(p + 1) * a.x_panel;
       stage_rows(stage, xA + o, hasB ? xB + o : nullptr, a.ld, tid, T);
     }
     cp_async_commit();
-    r16_first_pass<-1, float4, HALF>(buf, v, tid);
     {
       tm_wait_st();                             // the powers (and the zeroed sums) are stored
       float2 pw[16];
